@@ -1,0 +1,261 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+No GPU.  Every check here is independent of the oracle's own formulas:
+closed-form spectra, dense LAPACK brute force, exact invariants of the
+decomposition (Section 2.2-2.3, the Lemma on M^(k), Lemma 3.3) and
+hand-worked partitions.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import eig as E
+from oracle import mmd as MM
+from oracle import rng as R
+from oracle import solvers as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dirichlet_closed_form(m, dim):
+    k = np.arange(1, m + 1)
+    s = 4.0 * np.sin(np.pi * k / (2 * (m + 1))) ** 2
+    if dim == 2:
+        ev = s[:, None] + s[None, :]
+    else:
+        ev = s[:, None, None] + s[None, :, None] + s[None, None, :]
+    return np.sort(ev.ravel())
+
+
+# ------------------------------------------------------------------ inputs
+def test_fd_closed_form_2d_3d():
+    A = W.fd2d(12, const=True)
+    assert np.allclose(np.linalg.eigvalsh(A.dense()), dirichlet_closed_form(12, 2), atol=1e-12)
+    B = W.fd3d(6, const=True)
+    assert np.allclose(np.linalg.eigvalsh(B.dense()), dirichlet_closed_form(6, 3), atol=1e-12)
+
+
+def test_workload_sizes():
+    A = W.fd2d(64)
+    assert (A.n, A.nnz) == (4096, 20224)
+    A = W.fd3d(16)
+    assert A.n == 16**3 and A.nnz == 16**3 + 6 * 16 * 16 * 15
+
+
+def test_path_graph_spectrum():
+    n = 40
+    ev = np.linalg.eigvalsh(W.path_graph(n).dense())
+    k = np.arange(n)
+    assert np.allclose(ev, np.sort(2 - 2 * np.cos(np.pi * k / n)), atol=1e-12)
+
+
+# --------------------------------------------------------------------- rng
+def test_splitmix64_published_vector():
+    # SplitMix64 with state 0: the first outputs of the reference sequence.
+    # next() = mix(state += GAMMA); our stream key for seed S, stream s is
+    # mix(S + (s+1) GAMMA); with the raw mix we reproduce the sequence.
+    z = R._mix(np.arange(1, 4, dtype=np.uint64) * R.GAMMA)
+    assert [int(x) for x in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    u = R.uniform_pm1(7, 3, 1000)
+    assert u.min() >= -1 and u.max() < 1 and abs(u.mean()) < 0.1
+
+
+# --------------------------------------------------------------- partition
+def _csr_from_edges(n, edges):
+    e = np.asarray(edges)
+    return W.laplacian_from_edges(n, e[:, 0], e[:, 1], np.ones(len(e)), 1.0)
+
+
+def test_partition_golden():
+    cases = json.load(open(os.path.join(GOLDEN, "partition_cases.json")))["cases"]
+    for c in cases:
+        A = _csr_from_edges(c["n"], c["edges"])
+        po, pp, pr = MM.partition(A.rowptr, A.col, A.n, c["s_max"])
+        assert po.tolist() == c["patch_of"], c["name"]
+        assert pp.tolist() == c["patch_ptr"], c["name"]
+        assert pr.tolist() == c["patch_rows"], c["name"]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_partition_properties(seed):
+    A = W.random_spd_mmatrix(300, 6.0, seed)
+    po, pp, pr = MM.partition(A.rowptr, A.col, A.n, 4)
+    assert sorted(pr.tolist()) == list(range(A.n))
+    sizes = np.diff(pp)
+    assert sizes.min() >= 1 and sizes.max() <= 8
+    for j in range(len(sizes)):
+        assert np.all(po[pr[pp[j]:pp[j + 1]]] == j)
+        assert np.all(np.diff(pr[pp[j]:pp[j + 1]]) > 0)
+
+
+# ------------------------------------------------------------ decomposition
+@pytest.fixture(scope="module")
+def mmd_fd():
+    return MM.build(W.fd2d(24, seed=11), MM.BuildOpts(n_coarse=40))
+
+
+@pytest.fixture(scope="module")
+def mmd_graph():
+    return MM.build(W.torus_knn(1500, seed=5), MM.BuildOpts(n_coarse=60))
+
+
+@pytest.mark.parametrize("which", ["mmd_fd", "mmd_graph"])
+def test_mmd_invariants(which, request):
+    D = request.getfixturevalue(which)
+    assert D.K >= 2
+    Mprev = None
+    for k, lev in enumerate(D.levels, 1):
+        Phi = MM.Phi_matrix(lev).toarray()
+        Psi = lev.psi.toarray()
+        # Phi has orthonormal columns; Phi^T Psi = I (Section 2.2, correlation condition)
+        assert np.allclose(Phi.T @ Phi, np.eye(lev.n), atol=1e-12)
+        assert np.allclose(Phi.T @ Psi, np.eye(lev.n), atol=1e-10)
+        # A^(k) = Psi^T A^(k-1) Psi and M^(k) = Psi^T M^(k-1) Psi, symmetric
+        Aprev = D.A(k - 1).toarray()
+        assert np.allclose(lev.A.toarray(), Psi.T @ Aprev @ Psi, rtol=1e-12, atol=1e-12 * abs(Aprev).max())
+        Mp = np.eye(lev.n_fine) if Mprev is None else Mprev
+        assert np.allclose(lev.M.toarray(), Psi.T @ Mp @ Psi, atol=1e-12)
+        # lambda_min(M^(k)) >= 1 (Lemma on M^(k), Section 4)
+        assert np.linalg.eigvalsh(lev.M.toarray())[0] >= 1 - 1e-10
+        # lambda_min(A_st) >= lambda_min(A) (Theorem 2.2)
+        assert np.linalg.eigvalsh(lev.A.toarray())[0] >= np.linalg.eigvalsh(Aprev)[0] * (1 - 1e-10)
+        # Householder completion: [phi_j, U_j] orthonormal on each patch (Section 2.3)
+        for j in range(0, lev.n, max(1, lev.n // 20)):
+            a, b = lev.patch_ptr[j], lev.patch_ptr[j + 1]
+            u = lev.uhat[a:b]
+            H = np.eye(b - a) - 2 * np.outer(u, u)
+            assert np.allclose(H @ H.T, np.eye(b - a), atol=1e-13)
+            assert np.allclose(abs(H[:, 0]), abs(lev.phi[a:b]), atol=1e-13)
+            assert np.allclose(lev.phi[a:b] @ H[:, 1:], 0, atol=1e-13)
+        # U^T U = I and U^T Phi = 0 through the apply routines
+        g = np.random.default_rng(k).standard_normal((lev.n_fine - lev.n, 3))
+        y = MM.U_apply(lev, g)
+        assert np.allclose(y.T @ y, g.T @ g, atol=1e-12)
+        assert np.allclose(Phi.T @ y, 0, atol=1e-12)
+        x = np.random.default_rng(k + 7).standard_normal(lev.n_fine)
+        assert np.allclose(MM.Ut_apply(lev, x), (MM.U_apply(lev, np.eye(lev.n_fine - lev.n))).T @ x, atol=1e-12)
+        Mprev = lev.M.toarray()
+
+
+@pytest.mark.parametrize("which", ["mmd_fd", "mmd_graph"])
+def test_theta_chain_monotone(which, request):
+    """Lemma 3.3: A^{-1} = Theta^(0) >= Theta^(1) >= ... (so mu_i^(k) <= mu_i^(k-1))."""
+    D = request.getfixturevalue(which)
+    prev = 1.0 / np.linalg.eigvalsh(D.A0.toarray())  # descending mu
+    for k, lev in enumerate(D.levels, 1):
+        lam = sla.eigh(lev.A.toarray(), lev.M.toarray(), eigvals_only=True)
+        mu = 1.0 / lam
+        assert np.all(mu <= prev[:len(mu)] * (1 + 1e-9))
+        prev = mu
+
+
+def test_exact_psi_compression_bound():
+    """Theorem 2.1 with the exact Psi = A^{-1} Phi (Phi^T A^{-1} Phi)^{-1}: ||A^{-1} - Theta|| <= eps(P)."""
+    A = W.fd2d(12, seed=3)
+    D = MM.build(A, MM.BuildOpts(n_coarse=10, k_max=1))
+    lev = D.levels[0]
+    Ad = A.dense()
+    Ai = np.linalg.inv(Ad)
+    Phi = MM.Phi_matrix(lev).toarray()
+    Psi = Ai @ Phi @ np.linalg.inv(Phi.T @ Ai @ Phi)
+    Theta = Psi @ np.linalg.inv(Psi.T @ Ad @ Psi) @ Psi.T
+    assert np.linalg.norm(Ai - Theta, 2) <= lev.eps * (1 + 1e-10)
+    # Theorem 2.2 upper bound: lambda_max(A_st) <= delta(P)
+    assert np.linalg.eigvalsh(Psi.T @ Ad @ Psi)[-1] <= lev.delta * (1 + 1e-10)
+
+
+# ------------------------------------------------------------------ solvers
+def test_cg_fpcg_bsolve():
+    A = W.random_spd_mmatrix(400, 6.0, 4, shift=0.1).to_scipy()
+    b = np.random.default_rng(0).standard_normal(400)
+    xs = np.linalg.solve(A.toarray(), b)
+    x, it, ok = S.cg(A, b, tol=1e-12)
+    assert ok and np.linalg.norm(x - xs) <= 1e-9 * np.linalg.norm(xs)
+    D = MM.build(W.random_spd_mmatrix(400, 6.0, 4, shift=0.1), MM.BuildOpts(n_coarse=20, k_max=1))
+    lev = D.levels[0]
+    Ak, Mk = lev.A, lev.M
+    bk = np.random.default_rng(1).standard_normal(lev.n)
+    x, it, ok = S.fpcg(Ak, bk, Mk, None, 1e-12)
+    assert ok and np.allclose(x, np.linalg.solve(Ak.toarray(), bk), rtol=1e-8, atol=1e-10)
+    y = S.op(Ak, Mk, bk, 1e-12)
+    assert np.allclose(y, np.linalg.solve(Ak.toarray(), Mk @ bk), rtol=1e-8, atol=1e-10)
+    U = MM.U_apply(lev, np.eye(lev.n_fine - lev.n))
+    B = U.T @ A.toarray() @ U
+    r = np.random.default_rng(2).standard_normal(B.shape[0])
+    g = S.bsolve(A, lev, r, 1e-12)
+    assert np.allclose(g, np.linalg.solve(B, r), rtol=1e-8, atol=1e-10)
+    # Lemma 2.3 with kappa(U^T U) = 1: lambda_min(B) >= 1/eps(P)
+    assert np.linalg.eigvalsh(B)[0] >= 1.0 / lev.eps * (1 - 1e-10)
+
+
+# ------------------------------------------------------------------ Lanczos
+def test_m_lanczos_arnoldi_relation_and_restart():
+    """Section 4: A^{-1} M V = V T + f e^T, V^T M V = I, T symmetric tridiagonal;
+    Algorithm 2 keeps the relation and the k largest Ritz values survive."""
+    D = MM.build(W.fd2d(16, seed=9), MM.BuildOpts(n_coarse=20, k_max=1))
+    lev = D.levels[0]
+    A, M = lev.A, lev.M
+    Ad, Md = A.toarray(), M.toarray()
+    opf = lambda x: np.linalg.solve(Ad, Md @ x)
+    Vini = np.zeros((lev.n, 0))
+    lz = E.Lanczos(M, Vini, R.uniform_pm1(1, 0, lev.n), 1, 1, 1e-10)
+    for _ in range(12):
+        lz.step(opf)
+    V, T, f = lz.V, lz.T(), lz.f
+    e = np.zeros(12)
+    e[-1] = 1
+    rel = opf(V) - V @ T - np.outer(f, e)
+    assert np.abs(rel).max() <= 1e-10 * np.abs(opf(V)).max()
+    assert np.allclose(V.T @ Md @ V, np.eye(12), atol=1e-12)
+    assert np.allclose(V.T @ Md @ f, 0, atol=1e-10 * np.linalg.norm(f))
+    th_full = np.linalg.eigvalsh(T)
+    lz.restart(8, 4)
+    V, T, f = lz.V, lz.T(), lz.f
+    e = np.zeros(8)
+    e[-1] = 1
+    rel = opf(V) - V @ T - np.outer(f, e)
+    assert np.abs(rel).max() <= 1e-8 * np.abs(opf(V)).max()
+    assert np.allclose(V.T @ Md @ V, np.eye(8), atol=1e-10)
+    assert np.allclose(np.sort(np.linalg.eigvalsh(T)), np.sort(th_full)[4:], rtol=1e-8)
+
+
+# ------------------------------------------------------------ end to end
+def _check_eig(A, N, tol, opts=None, bopts=None):
+    D = MM.build(A, bopts or MM.BuildOpts(n_coarse=40))
+    r = E.eig_leftmost(D, N, tol, opts)
+    ev, evec = np.linalg.eigh(A.dense())
+    nrm = ev[-1]
+    assert np.all(np.abs(r.lam - ev[:N]) <= 1e-9 * np.maximum(np.abs(ev[:N]), 1e-9 * nrm) + 1e-12 * nrm)
+    res = E.residuals(A.to_scipy(), r.lam, r.V)
+    assert res.max() <= 10 * tol * nrm
+    assert np.allclose(r.V.T @ r.V, np.eye(N), atol=1e-8)
+    return D, r
+
+
+def test_eig_fd2d_small():
+    _check_eig(W.fd2d(20, seed=21), 12, 1e-10)
+
+
+def test_eig_const_laplacian_clusters():
+    """a == 1: the Dirichlet spectrum has exact double eigenvalues (k1 <-> k2)."""
+    A = W.fd2d(18, const=True)
+    D, r = _check_eig(A, 10, 1e-10)
+    assert np.allclose(r.lam, dirichlet_closed_form(18, 2)[:10], rtol=1e-9)
+
+
+def test_eig_graph_components():
+    """Shifted graph Laplacian: eigenvalue 1e-6 has multiplicity = #components."""
+    A1 = W.rgg(500, deg=8.0, seed=31)
+    A2 = W.rgg(400, deg=8.0, seed=32)
+    n = A1.n + A2.n
+    Asp = sp.block_diag([A1.to_scipy(), A2.to_scipy()]).tocsr()
+    A = W.CSR(n, Asp.indptr.astype(np.int32), Asp.indices.astype(np.int32), Asp.data)
+    from scipy.sparse.csgraph import connected_components
+    ncomp = connected_components(Asp, directed=False)[0]
+    D, r = _check_eig(A, ncomp + 4, 1e-9)
+    assert np.sum(np.abs(r.lam - 1e-6) < 1e-9) == ncomp
