@@ -294,6 +294,7 @@ class EigResult:
     counters: Counters
     levels: list
     mu1: float
+    trace: list = dataclasses.field(default_factory=list)  # (k, mu values output on level k)
 
 
 def eig_leftmost(D: _mmd.MMD, N: int, tol: float, opts: EigOpts | None = None) -> EigResult:
@@ -310,8 +311,7 @@ def eig_leftmost(D: _mmd.MMD, N: int, tol: float, opts: EigOpts | None = None) -
     AK = D.A(K).toarray()
     MK = np.eye(AK.shape[0]) if K == 0 else D.M(K).toarray()
     lam, Z = sla.eigh(AK, MK)
-    mu = 1.0 / lam[::-1]
-    Z = Z[:, ::-1]
+    mu = 1.0 / lam  # lambda ascending -> mu descending, columns of Z in the same order
     mu1 = float(mu[0])
     if K == 0:
         V, lam_out = Z[:, :N], 1.0 / mu[:N]
@@ -320,6 +320,7 @@ def eig_leftmost(D: _mmd.MMD, N: int, tol: float, opts: EigOpts | None = None) -
     keep = min(int(np.sum(mu >= opts.beta * epsK)), N)
     Vh, Dh = Z[:, :keep], mu[:keep]
     lstats.append(LevelStats(K, D.N(K), m_extended=keep))
+    trace = [(K, Dh.copy())]
     stream = 1000
     for k in range(K - 1, -1, -1):
         st = LevelStats(k, D.N(k))
@@ -346,8 +347,11 @@ def eig_leftmost(D: _mmd.MMD, N: int, tol: float, opts: EigOpts | None = None) -
         Vh, Dh = extend(Ah, Mh, Vh, Dh, pcg_tol, res_ok, mu_ex, d, N, opts, ctr, st, stream)
         stream += 1000
         lstats.append(st)
+        trace.append((k, Dh.copy()))
     order = np.argsort(-Dh, kind="stable")[:N]
-    return _finish(1.0 / Dh[order], Vh[:, order], ctr, lstats, mu1)
+    res = _finish(1.0 / Dh[order], Vh[:, order], ctr, lstats, mu1)
+    res.trace = trace
+    return res
 
 
 def _finish(lam, V, ctr, lstats, mu1):

@@ -259,3 +259,22 @@ def test_eig_graph_components():
     ncomp = connected_components(Asp, directed=False)[0]
     D, r = _check_eig(A, ncomp + 4, 1e-9)
     assert np.sum(np.abs(r.lam - 1e-6) < 1e-9) == ncomp
+
+
+def test_eig_level_outputs_are_top_of_each_pencil():
+    """Algorithm 6: each level outputs eigenpairs of its own operator
+    (A^(k))^{-1} M^(k) with the LARGEST mu (Lemma 3.2), to the level's accuracy
+    eps_k (Lemma 3.3); the coarsest level keeps mu >= beta eps_K."""
+    A = W.torus_knn(2500, seed=W.BASE_SEED + 40)
+    D = MM.build(A, MM.BuildOpts(n_coarse=80))
+    r = E.eig_leftmost(D, 20, 1e-8)
+    assert D.K >= 2 and len(r.trace) == D.K + 1
+    for k, mu in r.trace:
+        if len(mu) == 0:
+            continue
+        Ak = D.A(k).toarray()
+        Mk = np.eye(Ak.shape[0]) if k == 0 else D.M(k).toarray()
+        top = 1.0 / sla.eigh(Ak, Mk, eigvals_only=True)[: len(mu)]
+        assert np.all(np.diff(mu) <= 1e-12 * mu[0]), "descending"
+        tol = 1e-8 * top[0] if k == 0 else D.levels[k - 1].eps
+        assert np.abs(np.sort(mu)[::-1] - top).max() <= tol, k
