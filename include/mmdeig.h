@@ -1,0 +1,197 @@
+/*
+ * mmdeig.h -- C ABI of a GB300 (sm_103a) implementation of the hierarchically
+ * preconditioned eigensolver of Hou, Huang, Lam and Zhang, "A Fast
+ * Hierarchically Preconditioned Eigensolver Based on Multiresolution Matrix
+ * Decomposition" (arXiv 1804.03415).
+ *
+ * The library computes the N leftmost eigenpairs of a sparse symmetric
+ * positive definite matrix A.  It first builds a Multiresolution Matrix
+ * Decomposition (Section 2.3: levels A^(k) = Psi^(k)^T A^(k-1) Psi^(k),
+ * M^(k) = Psi^(k)^T M^(k-1) Psi^(k), complement bases U^(k)), then runs the
+ * Hierarchical Eigenpair Computation (Algorithm 6): a dense generalized
+ * eigenproblem on the coarsest level, then per level an Eigenpair Refinement
+ * (Algorithm 5) and an Eigenpair Extension (Algorithm 4, implicitly restarted
+ * M-Lanczos, Algorithms 2-3), whose operator is Operator OP: PCG on A^(k)
+ * preconditioned by M^(k) (Section 4).  The loop continues to level 0
+ * (A^(0) = A, M^(0) = I) so that the result meets a residual target.
+ *
+ * Conventions for every entry point:
+ *   - Return value: MMD_OK (0) or a negative MMD_E* code; no exception or
+ *     C++ type crosses the boundary.  mmd_strerror() names a code and
+ *     mmd_last_error() gives a message for the calling thread's last failure.
+ *   - Sparse input: full symmetric CSR storage (both triangles), int32 row
+ *     pointers and column indices sorted ascending within each row, FP64
+ *     values, diagonal present.  Pointers are host memory unless the struct's
+ *     on_device flag is 1 (device memory of the current CUDA device).
+ *     Inputs are borrowed for the duration of the call only.
+ *   - Dense outputs are caller-allocated, column-major.  *_on_device flags say
+ *     whether an output pointer is device memory.
+ *   - Streams: work is enqueued on the cudaStream_t passed as void*
+ *     (NULL = legacy default stream); every entry point synchronises that
+ *     stream before it returns.
+ *   - Handles are not thread-safe: one call at a time per handle.
+ */
+#ifndef MMDEIG_H
+#define MMDEIG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define MMD_OK 0
+#define MMD_EINVAL (-1)   /* bad argument or malformed CSR */
+#define MMD_ENOTSPD (-2)  /* a Cholesky/energy found a non-SPD matrix */
+#define MMD_ENOCONV (-3)  /* an iteration cap was hit; partial results returned */
+#define MMD_ETIMEOUT (-4) /* a device-side wait exceeded its time limit */
+#define MMD_ECUDA (-5)    /* a CUDA runtime call failed */
+#define MMD_ENOMEM (-6)   /* host or device allocation failed */
+
+/* precision modes of eig_leftmost */
+#define MMD_FP64 0  /* every step in FP64 */
+#define MMD_MIXED 1 /* FP32 inner solves, FP64 outer residual and refinement */
+
+typedef struct mmd_handle mmd_handle;
+
+typedef struct {
+  int64_t n;             /* rows = columns */
+  int64_t nnz;           /* stored entries (both triangles) */
+  const int32_t* rowptr; /* n + 1 */
+  const int32_t* col;    /* nnz, ascending per row */
+  const double* val;     /* nnz */
+  int on_device;         /* 1: the three arrays are device pointers */
+} mmd_csr;
+
+/* Decomposition build options (the patch construction is this library's
+ * reading of Section 2.2: integer-only aggregation of the matrix pattern,
+ * interior-energy phi, localized psi on whole neighbouring patches). */
+typedef struct {
+  int s_max;      /* pass-1 patch size cap; joins allowed up to 2*s_max (default 8) */
+  int omega_max;  /* row cap of a psi support neighbourhood (default 256) */
+  int loc_radius; /* 0: support = own patch, 1: plus neighbouring patches (default 1) */
+  int n_coarse;   /* stop when N^(k) <= n_coarse (default 300) */
+  int k_max;      /* maximum number of levels (default 8) */
+  int device;     /* 1: upload the levels to the current CUDA device (default);
+                     0: host-only handle (inspection with mmd_level_info only) */
+  int threads;    /* host threads for the build, 0 = all cores */
+} mmd_build_opts;
+
+/* Solver options (Section 6 parameter rules). */
+typedef struct {
+  double alpha;        /* refinement threshold mu_re^(k) = alpha eps_{k+1} (default 3) */
+  double beta;         /* extension threshold mu_ex^(k) = beta eps_k (default 1) */
+  int d;               /* searching step, 0 = min(N^(k)/10, N/10) clamped to >= 1 */
+  int c_r;             /* restart factor: p = c_r * d shifts (default 1) */
+  int precision;       /* MMD_FP64 or MMD_MIXED */
+  int max_cg_iter;     /* cap per CG/PCG call (default 20000) */
+  int max_restarts;    /* cap per convergence loop (default 400) */
+  int max_refine_iter; /* cap of Algorithm 5 iterations (default 100) */
+  double timeout_s;    /* per device-side wait (default 2 s) */
+  uint64_t seed;       /* SplitMix64 seed of the random vectors drawn */
+  void* stream;        /* cudaStream_t */
+  int profile;         /* 1: time every launch of the PCG kernel with events */
+} mmd_eig_opts;
+
+/* Counters and timings of one eig_leftmost call (Section 7 reports the same
+ * kinds of counters: PCG/CG calls and iterations, refinement iterations). */
+typedef struct {
+  int64_t op_calls, pcg_iters, inner_iters;      /* Operator OP (Alg 3 line 7) */
+  int64_t b_calls, b_iters;                      /* CG on B^(k) (Alg 5) */
+  int64_t refine_pcg_calls, refine_pcg_iters;    /* warm-started PCG in Alg 5 */
+  int64_t restarts, lanczos_steps, refine_iters; /* Alg 2, Alg 3, Alg 5 */
+  int64_t not_converged;                         /* capped loops */
+  int64_t kernel_launches;                       /* CUDA kernels launched */
+  int n_levels;                                  /* K + 1 */
+  int n_converged;                               /* pairs meeting the residual target */
+  double norm_A;                                 /* ||A||_inf, upper bound of ||A||_2 */
+  double max_rel_residual;                       /* max ||Av - lv||_2 / ||A||_inf */
+  double mu1;                                    /* largest mu found on the coarsest level */
+  double t_total_ms;
+  /* profile == 1: the sparse-solver kernel's launches */
+  int64_t pcg_launches;
+  double pcg_ms;        /* sum of event-timed durations */
+  double pcg_bytes;     /* algorithmic bytes moved by those launches */
+} mmd_eig_stats;
+
+/* Read-only view of level k (1 <= k <= K) of a handle; host pointers owned by
+ * the handle, valid until mmd_free.  Arrays follow the natural (build) order:
+ * patches in creation order, rows ascending within a patch. */
+typedef struct {
+  int64_t n_fine;            /* N^(k-1) */
+  int64_t n;                 /* N^(k) = number of patches */
+  const int32_t* patch_of;   /* n_fine */
+  const int32_t* patch_ptr;  /* n + 1 */
+  const int32_t* patch_rows; /* n_fine */
+  const double* phi;         /* n_fine, aligned with patch_rows */
+  const int32_t* omega_ptr;  /* n + 1: support of psi_j */
+  const int32_t* omega_rows; /* omega_ptr[n] */
+  int64_t psi_nnz;           /* Psi^(k): N^(k-1) x N^(k), CSR */
+  const int32_t* psi_rowptr;
+  const int32_t* psi_col;
+  const double* psi_val;
+  int64_t a_nnz;             /* A^(k), CSR */
+  const int32_t* a_rowptr;
+  const int32_t* a_col;
+  const double* a_val;
+  int64_t m_nnz;             /* M^(k), CSR */
+  const int32_t* m_rowptr;
+  const int32_t* m_col;
+  const double* m_val;
+  double eps;                /* error factor eps(P^(k)), Section 2.2 */
+  double delta;              /* condition factor delta(P^(k)), Theorem 2.2 */
+  int used_closed;           /* patches whose interior energy was not PSD */
+} mmd_level_view;
+
+void mmd_default_build_opts(mmd_build_opts* o);
+void mmd_default_eig_opts(mmd_eig_opts* o);
+
+/* Build the decomposition of A (Section 2.3).  A is copied; *out owns every
+ * level (host arrays, and device arrays when opts->device = 1).
+ * Errors: MMD_EINVAL (n < 1, unsorted/duplicate/out-of-range columns, missing
+ * diagonal, asymmetric pattern or values), MMD_ENOTSPD (a local energy or
+ * neighbourhood matrix is not positive definite), MMD_ENOMEM, MMD_ECUDA. */
+int mmd_build(const mmd_csr* A, const mmd_build_opts* opts, mmd_handle** out);
+
+/* Number of levels K (the handle holds levels 0..K). */
+int mmd_num_levels(const mmd_handle* h);
+
+/* Size N^(k) of level k (0 <= k <= K), or a negative code. */
+int64_t mmd_level_size(const mmd_handle* h, int k);
+
+/* Fill *out with read-only views of level k, 1 <= k <= K. */
+int mmd_level_info(const mmd_handle* h, int k, mmd_level_view* out);
+
+/* N leftmost eigenpairs of A (Algorithm 6 with the level-0 completion).
+ * tol: relative residual target ||A v - lambda v||_2 <= tol ||A||.
+ * lambda: N values ascending; V: n x N column-major, 2-norm orthonormal
+ * columns, sign so that the largest-|.| entry is positive.  lambda and V are
+ * host or device memory per outputs_on_device.  stats may be NULL.
+ * Requires a device handle.  MMD_ENOCONV returns the best pairs found. */
+int eig_leftmost(mmd_handle* h, int N, double tol, const mmd_eig_opts* opts,
+                 double* lambda, double* V, int outputs_on_device,
+                 mmd_eig_stats* stats);
+
+/* Level operators on device vectors of level k, in the natural (build) order
+ * of that level, for tests and kernel benchmarks.
+ * mmd_level_spmv: y = A^(k) x (which = 0) or M^(k) x (which = 1, k >= 1).
+ * mmd_level_op: y = OP(x) = pcg(A^(k), M^(k) x, M^(k), 0, tol) (the Operator
+ *   OP box after Algorithm 3); k = 0 uses M = I (plain CG).  iters may be NULL.
+ * mmd_level_bsolve: x = U g where g = CG(B^(k), U^T M^(k-1) q, tol) and
+ *   B^(k) = U^(k)^T A^(k-1) U^(k) (Algorithm 5, first loop); q and x are
+ *   level-(k-1) vectors, 1 <= k <= K. */
+int mmd_level_spmv(mmd_handle* h, int k, int which, const double* x, double* y, void* stream);
+int mmd_level_op(mmd_handle* h, int k, const double* x, double* y, double tol, int max_iter,
+                 int64_t* iters, void* stream);
+int mmd_level_bsolve(mmd_handle* h, int k, const double* q, double* x, double tol, int max_iter,
+                     int64_t* iters, void* stream);
+
+void mmd_free(mmd_handle* h);
+const char* mmd_strerror(int code);
+const char* mmd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

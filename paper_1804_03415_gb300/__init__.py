@@ -1,0 +1,140 @@
+"""GB300 (sm_103a) hierarchically preconditioned eigensolver (arXiv 1804.03415).
+
+Python face of ``libmmdeig.so``; every call marshals arguments into the C ABI
+declared in ``include/mmdeig.h``.  All arithmetic runs in the library's CUDA
+kernels (and, for the decomposition build, its host C++); nothing here falls
+back to Python or PyTorch arithmetic.
+
+    A  = workloads.torus_knn(20000)             # any symmetric CSR
+    h  = MMD(A.rowptr, A.col, A.val)            # mmd_build
+    lam, V, stats = h.eig_leftmost(50, 1e-8)    # eig_leftmost
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import MMD_FP64, MMD_MIXED, MMDError  # noqa: F401
+
+
+def build_opts(**kw) -> _lib.mmd_build_opts:
+    lib = _lib.load()
+    o = _lib.mmd_build_opts()
+    lib.mmd_default_build_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def eig_opts(**kw) -> _lib.mmd_eig_opts:
+    lib = _lib.load()
+    o = _lib.mmd_eig_opts()
+    lib.mmd_default_eig_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class MMD:
+    """Handle of a Multiresolution Matrix Decomposition (mmd_build / mmd_free)."""
+
+    def __init__(self, rowptr, col, val, device: bool = True, **opts):
+        lib = _lib.load()
+        on_dev = 0
+        if hasattr(rowptr, "data_ptr"):  # torch tensors on the GPU
+            on_dev = 1 if rowptr.is_cuda else 0
+        if on_dev:
+            n = rowptr.numel() - 1
+            nnz = col.numel()
+            ptrs = (rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
+            self._keep = (rowptr, col, val)
+        else:
+            rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            val = np.ascontiguousarray(val, dtype=np.float64)
+            n, nnz = len(rowptr) - 1, len(col)
+            ptrs = (rowptr.ctypes.data, col.ctypes.data, val.ctypes.data)
+            self._keep = (rowptr, col, val)
+        csr = _lib.mmd_csr(n, nnz, ptrs[0], ptrs[1], ptrs[2], on_dev)
+        bo = build_opts(device=1 if device else 0, **opts)
+        h = C.c_void_p()
+        _lib.check(lib.mmd_build(C.byref(csr), C.byref(bo), C.byref(h)), "mmd_build")
+        self.h = h
+        self.n = n
+        self.nnz = nnz
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.mmd_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_levels(self) -> int:
+        return self._lib.mmd_num_levels(self.h)
+
+    def level_size(self, k: int) -> int:
+        return int(self._lib.mmd_level_size(self.h, k))
+
+    def level(self, k: int) -> dict:
+        """Copies of level k's arrays (natural order), 1 <= k <= K."""
+        v = _lib.mmd_level_view()
+        _lib.check(self._lib.mmd_level_info(self.h, k, C.byref(v)), "mmd_level_info")
+
+        def arr(p, n, dt):
+            return np.ctypeslib.as_array(p, shape=(int(n),)).astype(dt, copy=True)
+
+        nf, n = v.n_fine, v.n
+        return {
+            "n_fine": nf, "n": n,
+            "patch_of": arr(v.patch_of, nf, np.int32), "patch_ptr": arr(v.patch_ptr, n + 1, np.int32),
+            "patch_rows": arr(v.patch_rows, nf, np.int32), "phi": arr(v.phi, nf, np.float64),
+            "omega_ptr": arr(v.omega_ptr, n + 1, np.int32),
+            "omega_rows": arr(v.omega_rows, arr(v.omega_ptr, n + 1, np.int32)[-1], np.int32),
+            "psi": (arr(v.psi_rowptr, nf + 1, np.int32), arr(v.psi_col, v.psi_nnz, np.int32),
+                    arr(v.psi_val, v.psi_nnz, np.float64)),
+            "A": (arr(v.a_rowptr, n + 1, np.int32), arr(v.a_col, v.a_nnz, np.int32), arr(v.a_val, v.a_nnz, np.float64)),
+            "M": (arr(v.m_rowptr, n + 1, np.int32), arr(v.m_col, v.m_nnz, np.int32), arr(v.m_val, v.m_nnz, np.float64)),
+            "eps": v.eps, "delta": v.delta, "used_closed": v.used_closed,
+        }
+
+    # ---- level operators on CUDA tensors (torch) in natural order
+    def level_spmv(self, k, which, x, y, stream=0):
+        _lib.check(self._lib.mmd_level_spmv(self.h, k, which, x.data_ptr(), y.data_ptr(), stream), "mmd_level_spmv")
+
+    def level_op(self, k, x, y, tol, max_iter=20000, stream=0) -> int:
+        it = C.c_int64(0)
+        _lib.check(self._lib.mmd_level_op(self.h, k, x.data_ptr(), y.data_ptr(), tol, max_iter, C.byref(it), stream),
+                   "mmd_level_op")
+        return it.value
+
+    def level_bsolve(self, k, q, x, tol, max_iter=20000, stream=0) -> int:
+        it = C.c_int64(0)
+        _lib.check(self._lib.mmd_level_bsolve(self.h, k, q.data_ptr(), x.data_ptr(), tol, max_iter, C.byref(it),
+                                              stream), "mmd_level_bsolve")
+        return it.value
+
+    def eig_leftmost(self, N: int, tol: float, out=None, allow_noconv: bool = False, **opts):
+        """N smallest eigenpairs.  ``out``: None (host numpy) or (lam, V) CUDA tensors."""
+        o = eig_opts(**opts)
+        st = _lib.mmd_eig_stats()
+        if out is None:
+            lam = np.zeros(N)
+            V = np.zeros((N, self.n))  # column-major n x N == row-major N x n
+            rc = self._lib.eig_leftmost(self.h, N, tol, C.byref(o), lam.ctypes.data, V.ctypes.data, 0, C.byref(st))
+            res = (lam, V.T)
+        else:
+            lam_t, V_t = out
+            rc = self._lib.eig_leftmost(self.h, N, tol, C.byref(o), lam_t.data_ptr(), V_t.data_ptr(), 1, C.byref(st))
+            res = (lam_t, V_t)
+        if rc != _lib.MMD_OK and not (allow_noconv and rc == _lib.MMD_ENOCONV):
+            _lib.check(rc, "eig_leftmost")
+        return res[0], res[1], st.as_dict()

@@ -1,0 +1,372 @@
+// C ABI of the library: handles, device upload, level operators.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "driver.h"
+#include "kernels.h"
+#include "mmd_internal.h"
+
+namespace mmd {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+template <typename T>
+static int dalloc(T** p, size_t n) {
+  if (n == 0) n = 1;
+  if (cudaMalloc((void**)p, n * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed");
+    return MMD_ENOMEM;
+  }
+  return MMD_OK;
+}
+
+template <typename T>
+static int dput(T** p, const std::vector<T>& v) {
+  int rc = dalloc(p, v.size());
+  if (rc) return rc;
+  if (!v.empty() && cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+    set_error("cudaMemcpy to device failed");
+    return MMD_ECUDA;
+  }
+  return MMD_OK;
+}
+
+// Permute a square CSR symmetrically: new row i' = old perm[i'], columns by iperm.
+static HCSR permute_sym(const HCSR& A, const std::vector<int32_t>& perm, const std::vector<int32_t>& iperm) {
+  HCSR B;
+  B.nrows = A.nrows;
+  B.ncols = A.ncols;
+  B.rowptr.assign(A.nrows + 1, 0);
+  for (int64_t i = 0; i < A.nrows; ++i) B.rowptr[i + 1] = B.rowptr[i] + (A.rowptr[perm[i] + 1] - A.rowptr[perm[i]]);
+  B.col.resize(A.col.size());
+  B.val.resize(A.val.size());
+  std::vector<std::pair<int32_t, double>> row;
+  for (int64_t i = 0; i < A.nrows; ++i) {
+    const int32_t r = perm[i];
+    row.clear();
+    for (int32_t k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k) row.push_back({iperm[A.col[k]], A.val[k]});
+    std::sort(row.begin(), row.end());
+    for (size_t t = 0; t < row.size(); ++t) {
+      B.col[B.rowptr[i] + t] = row[t].first;
+      B.val[B.rowptr[i] + t] = row[t].second;
+    }
+  }
+  return B;
+}
+
+// Rows permuted by prow (new i' = old prow[i']), columns renumbered by icol.
+static HCSR permute_rect(const HCSR& A, const std::vector<int32_t>& prow, const std::vector<int32_t>& icol) {
+  HCSR B;
+  B.nrows = A.nrows;
+  B.ncols = A.ncols;
+  B.rowptr.assign(A.nrows + 1, 0);
+  for (int64_t i = 0; i < A.nrows; ++i) B.rowptr[i + 1] = B.rowptr[i] + (A.rowptr[prow[i] + 1] - A.rowptr[prow[i]]);
+  B.col.resize(A.col.size());
+  B.val.resize(A.val.size());
+  std::vector<std::pair<int32_t, double>> row;
+  for (int64_t i = 0; i < A.nrows; ++i) {
+    const int32_t r = prow[i];
+    row.clear();
+    for (int32_t k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k) row.push_back({icol[A.col[k]], A.val[k]});
+    std::sort(row.begin(), row.end());
+    for (size_t t = 0; t < row.size(); ++t) {
+      B.col[B.rowptr[i] + t] = row[t].first;
+      B.val[B.rowptr[i] + t] = row[t].second;
+    }
+  }
+  return B;
+}
+
+static int upload_csr(const HCSR& A, DCSR& D) {
+  D.nrows = A.nrows;
+  D.ncols = A.ncols;
+  D.nnz = A.nnz();
+  int rc;
+  if ((rc = dput(&D.rowptr, A.rowptr))) return rc;
+  if ((rc = dput(&D.col, A.col))) return rc;
+  if ((rc = dput(&D.val, A.val))) return rc;
+  std::vector<float> v32(A.val.begin(), A.val.end());
+  if ((rc = dput(&D.val32, v32))) return rc;
+  D.mean_row = A.nrows ? double(D.nnz) / double(A.nrows) : 0.0;
+  int mx = 0;
+  for (int64_t i = 0; i < A.nrows; ++i) mx = std::max(mx, A.rowptr[i + 1] - A.rowptr[i]);
+  D.max_row = mx;
+  return MMD_OK;
+}
+
+static void free_csr(DCSR& D) {
+  cudaFree(D.rowptr);
+  cudaFree(D.col);
+  cudaFree(D.val);
+  cudaFree(D.val32);
+  D = DCSR();
+}
+
+int upload_levels(mmd_handle* h) {
+  const int K = (int)h->levels.size();
+  h->dl.assign(K + 1, DLevel());
+  // device order of level k: patches of level k+1 (natural patch ids), rows ascending inside
+  std::vector<std::vector<int32_t>> perm(K + 1), iperm(K + 1);
+  for (int k = 0; k <= K; ++k) {
+    const int64_t n = (k == 0) ? h->A0.nrows : h->levels[k - 1].n;
+    if (k < K)
+      perm[k] = h->levels[k].patch_rows;
+    else {
+      perm[k].resize(n);
+      for (int64_t i = 0; i < n; ++i) perm[k][i] = (int32_t)i;
+    }
+    iperm[k].resize(n);
+    for (int64_t i = 0; i < n; ++i) iperm[k][perm[k][i]] = (int32_t)i;
+  }
+  int rc;
+  for (int k = 0; k <= K; ++k) {
+    DLevel& L = h->dl[k];
+    const HCSR& A = (k == 0) ? h->A0 : h->levels[k - 1].A;
+    L.n = A.nrows;
+    if ((rc = upload_csr(permute_sym(A, perm[k], iperm[k]), L.A))) return rc;
+    if (k >= 1) {
+      const HLevel& H = h->levels[k - 1];
+      if ((rc = upload_csr(permute_sym(H.M, perm[k], iperm[k]), L.M))) return rc;
+      if ((rc = upload_csr(permute_rect(H.psi, perm[k - 1], iperm[k]), L.psi))) return rc;
+      L.eps = H.eps;
+      L.delta = H.delta;
+    }
+    if (k < K) {
+      const HLevel& N = h->levels[k];
+      L.nseg = N.n;
+      if ((rc = dput(&L.seg_ptr, N.patch_ptr))) return rc;
+      if ((rc = dput(&L.phi_next, N.phi))) return rc;
+    }
+    L.perm = perm[k];
+    if ((rc = dput(&L.d_perm, perm[k]))) return rc;
+    if ((rc = dput(&L.d_iperm, iperm[k]))) return rc;
+  }
+  return MMD_OK;
+}
+
+void free_device(mmd_handle* h) {
+  for (auto& L : h->dl) {
+    free_csr(L.A);
+    free_csr(L.M);
+    free_csr(L.psi);
+    cudaFree(L.seg_ptr);
+    cudaFree(L.phi_next);
+    cudaFree(L.d_perm);
+    cudaFree(L.d_iperm);
+  }
+  h->dl.clear();
+  free_workspace(h);
+}
+
+}  // namespace mmd
+
+using namespace mmd;
+
+extern "C" {
+
+void mmd_default_build_opts(mmd_build_opts* o) {
+  if (!o) return;
+  o->s_max = 8;
+  o->omega_max = 256;
+  o->loc_radius = 1;
+  o->n_coarse = 300;
+  o->k_max = 8;
+  o->device = 1;
+  o->threads = 0;
+}
+
+void mmd_default_eig_opts(mmd_eig_opts* o) {
+  if (!o) return;
+  o->alpha = 3.0;
+  o->beta = 1.0;
+  o->d = 0;
+  o->c_r = 1;
+  o->precision = MMD_FP64;
+  o->max_cg_iter = 20000;
+  o->max_restarts = 400;
+  o->max_refine_iter = 100;
+  o->timeout_s = 2.0;
+  o->seed = 20180409ull;
+  o->stream = nullptr;
+  o->profile = 0;
+}
+
+int mmd_build(const mmd_csr* A, const mmd_build_opts* opts, mmd_handle** out) {
+  if (!out) {
+    set_error("mmd_build: out is NULL");
+    return MMD_EINVAL;
+  }
+  *out = nullptr;
+  mmd_build_opts o;
+  mmd_default_build_opts(&o);
+  if (opts) o = *opts;
+  if (o.s_max < 1 || o.omega_max < 1 || o.n_coarse < 1 || o.k_max < 0 || o.loc_radius < 0) {
+    set_error("mmd_build: invalid build options");
+    return MMD_EINVAL;
+  }
+  if (!A) {
+    set_error("mmd_build: A is NULL");
+    return MMD_EINVAL;
+  }
+  mmd_handle* h = new (std::nothrow) mmd_handle();
+  if (!h) return MMD_ENOMEM;
+  h->bopts = o;
+  mmd_csr hostA = *A;
+  std::vector<int32_t> rp, ci;
+  std::vector<double> va;
+  if (A->on_device) {
+    if (A->n < 1 || A->nnz < 1) {
+      delete h;
+      set_error("mmd_build: bad sizes");
+      return MMD_EINVAL;
+    }
+    rp.resize(A->n + 1);
+    ci.resize(A->nnz);
+    va.resize(A->nnz);
+    if (cudaMemcpy(rp.data(), A->rowptr, rp.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(ci.data(), A->col, ci.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(va.data(), A->val, va.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      delete h;
+      set_error("mmd_build: copying the device CSR failed");
+      return MMD_ECUDA;
+    }
+    hostA.rowptr = rp.data();
+    hostA.col = ci.data();
+    hostA.val = va.data();
+    hostA.on_device = 0;
+  }
+  int rc;
+  try {
+    rc = build_host(&hostA, &o, h);
+  } catch (const std::bad_alloc&) {
+    rc = MMD_ENOMEM;
+    set_error("mmd_build: host allocation failed");
+  }
+  if (rc == MMD_OK && o.device) {
+    h->on_device = true;
+    cudaGetDevice(&h->device);
+    rc = upload_levels(h);
+  }
+  if (rc != MMD_OK) {
+    mmd_free(h);
+    return rc;
+  }
+  *out = h;
+  return MMD_OK;
+}
+
+int mmd_num_levels(const mmd_handle* h) { return h ? (int)h->levels.size() : MMD_EINVAL; }
+
+int64_t mmd_level_size(const mmd_handle* h, int k) {
+  if (!h || k < 0 || k > (int)h->levels.size()) return MMD_EINVAL;
+  return k == 0 ? h->A0.nrows : h->levels[k - 1].n;
+}
+
+int mmd_level_info(const mmd_handle* h, int k, mmd_level_view* v) {
+  if (!h || !v || k < 1 || k > (int)h->levels.size()) {
+    set_error("mmd_level_info: level out of range");
+    return MMD_EINVAL;
+  }
+  const HLevel& L = h->levels[k - 1];
+  v->n_fine = L.n_fine;
+  v->n = L.n;
+  v->patch_of = L.patch_of.data();
+  v->patch_ptr = L.patch_ptr.data();
+  v->patch_rows = L.patch_rows.data();
+  v->phi = L.phi.data();
+  v->omega_ptr = L.omega_ptr.data();
+  v->omega_rows = L.omega_rows.data();
+  v->psi_nnz = L.psi.nnz();
+  v->psi_rowptr = L.psi.rowptr.data();
+  v->psi_col = L.psi.col.data();
+  v->psi_val = L.psi.val.data();
+  v->a_nnz = L.A.nnz();
+  v->a_rowptr = L.A.rowptr.data();
+  v->a_col = L.A.col.data();
+  v->a_val = L.A.val.data();
+  v->m_nnz = L.M.nnz();
+  v->m_rowptr = L.M.rowptr.data();
+  v->m_col = L.M.col.data();
+  v->m_val = L.M.val.data();
+  v->eps = L.eps;
+  v->delta = L.delta;
+  v->used_closed = L.used_closed;
+  return MMD_OK;
+}
+
+void mmd_free(mmd_handle* h) {
+  if (!h) return;
+  if (h->on_device) free_device(h);
+  delete h;
+}
+
+const char* mmd_strerror(int code) {
+  switch (code) {
+    case MMD_OK: return "ok";
+    case MMD_EINVAL: return "invalid argument";
+    case MMD_ENOTSPD: return "matrix not symmetric positive definite";
+    case MMD_ENOCONV: return "iteration cap reached before convergence";
+    case MMD_ETIMEOUT: return "device wait timed out";
+    case MMD_ECUDA: return "CUDA error";
+    case MMD_ENOMEM: return "out of memory";
+    default: return "unknown error";
+  }
+}
+
+const char* mmd_last_error(void) { return g_last_error.c_str(); }
+
+int mmd_level_spmv(mmd_handle* h, int k, int which, const double* x, double* y, void* stream) {
+  if (!h || !h->on_device || k < 0 || k > (int)h->levels.size() || (which == 1 && k == 0) || !x || !y) {
+    set_error("mmd_level_spmv: bad arguments");
+    return MMD_EINVAL;
+  }
+  return level_spmv(h, k, which, x, y, (cudaStream_t)stream);
+}
+
+int mmd_level_op(mmd_handle* h, int k, const double* x, double* y, double tol, int max_iter, int64_t* iters,
+                 void* stream) {
+  if (!h || !h->on_device || k < 0 || k > (int)h->levels.size() || !x || !y || !(tol > 0) || max_iter < 1) {
+    set_error("mmd_level_op: bad arguments");
+    return MMD_EINVAL;
+  }
+  return level_op(h, k, x, y, tol, max_iter, iters, (cudaStream_t)stream);
+}
+
+int mmd_level_bsolve(mmd_handle* h, int k, const double* q, double* x, double tol, int max_iter, int64_t* iters,
+                     void* stream) {
+  if (!h || !h->on_device || k < 1 || k > (int)h->levels.size() || !q || !x || !(tol > 0) || max_iter < 1) {
+    set_error("mmd_level_bsolve: bad arguments");
+    return MMD_EINVAL;
+  }
+  return level_bsolve(h, k, q, x, tol, max_iter, iters, (cudaStream_t)stream);
+}
+
+int eig_leftmost(mmd_handle* h, int N, double tol, const mmd_eig_opts* opts, double* lambda, double* V,
+                 int outputs_on_device, mmd_eig_stats* stats) {
+  if (!h || !h->on_device) {
+    set_error("eig_leftmost: needs a device handle");
+    return MMD_EINVAL;
+  }
+  if (N < 1 || N > h->A0.nrows || !(tol > 0) || !lambda || !V) {
+    set_error("eig_leftmost: N must be in [1, n], tol > 0, outputs non-NULL");
+    return MMD_EINVAL;
+  }
+  mmd_eig_opts o;
+  mmd_default_eig_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.alpha > 0) || !(o.beta > 0) || o.c_r < 1 || o.max_cg_iter < 1 || o.max_restarts < 1 ||
+      o.max_refine_iter < 1 || !(o.timeout_s > 0) || (o.precision != MMD_FP64 && o.precision != MMD_MIXED)) {
+    set_error("eig_leftmost: invalid options");
+    return MMD_EINVAL;
+  }
+  return run_eig(h, N, tol, o, lambda, V, outputs_on_device, stats);
+}
+
+}  // extern "C"

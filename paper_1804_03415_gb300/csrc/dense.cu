@@ -1,0 +1,745 @@
+// Small dense FP64 kernels of the eigensolver: the tridiagonal Lanczos
+// matrix T (Algorithms 1-4), the implicit restart's shifted QR sweeps
+// (Algorithm 2), the Rayleigh-Ritz matrix S and the M-QR Cholesky factor of
+// the refinement (Algorithm 5) and the coarsest generalized eigenproblem
+// (Algorithm 6, first step).
+//
+// GB300 has little FP64 throughput per SM and long FP64 latencies, so the
+// classical sequential algorithms are restructured for parallel hardware:
+//   * tridiagonal eigenvalues: Sturm-sequence bisection, one thread per
+//     eigenvalue (Golub and Van Loan, Section 8.4);
+//   * tridiagonal eigenvectors: inverse iteration with a partially pivoted
+//     tridiagonal LU, one thread per cluster of close eigenvalues, modified
+//     Gram-Schmidt inside a cluster (Wilkinson's inverse iteration);
+//   * p shifted QR sweeps (implicit bulge chases, Golub and Van Loan Alg.
+//     8.3.2): the p bulges move down the matrix together, bulge j three
+//     positions behind bulge j-1, so one step of the schedule performs up to
+//     p independent rotations; the rotations are recorded and applied to Q by
+//     many blocks, one row of Q per thread;
+//   * dense symmetric eigenproblems: Householder tridiagonalisation on one
+//     block, then the two tridiagonal kernels and a parallel back-transform.
+#include <cuda_runtime.h>
+
+#include "dev_common.cuh"
+#include "kernels.h"
+
+namespace mmd {
+namespace {
+
+constexpr double kEps = 2.220446049250313e-16;
+
+// ------------------------------------------------------------ bisection
+__device__ int sturm_count(const double* d, const double* e2, int n, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0) ++cnt;
+  for (int k = 1; k < n; ++k) {
+    q = d[k] - x - e2[k - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0) ++cnt;
+  }
+  return cnt;  // number of eigenvalues < x
+}
+
+__global__ void tri_bounds_kernel(const double* d, const double* e, int n, double* bounds, double* e2) {
+  // bounds[0] = lo, bounds[1] = hi (Gershgorin), bounds[2] = pivmin
+  __shared__ double slo[256], shi[256], smx[256];
+  double lo = 1e300, hi = -1e300, mx = 0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double el = k > 0 ? fabs(e[k - 1]) : 0.0, er = k < n - 1 ? fabs(e[k]) : 0.0;
+    lo = fmin(lo, d[k] - el - er);
+    hi = fmax(hi, d[k] + el + er);
+    mx = fmax(mx, fmax(fabs(d[k]), er));
+    if (k < n - 1) e2[k] = e[k] * e[k];
+  }
+  slo[threadIdx.x] = lo;
+  shi[threadIdx.x] = hi;
+  smx[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + o]);
+      shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + o]);
+      smx[threadIdx.x] = fmax(smx[threadIdx.x], smx[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double span = fmax(shi[0] - slo[0], smx[0]);
+    bounds[0] = slo[0] - 4 * kEps * span - 1e-300;
+    bounds[1] = shi[0] + 4 * kEps * span + 1e-300;
+    bounds[2] = fmax(smx[0] * kEps * kEps, 1e-300);
+  }
+}
+
+__global__ void tri_bisect_kernel(const double* d, const double* e2, int n, const double* bounds, double* w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double lo = bounds[0], hi = bounds[1];
+  const double pivmin = bounds[2];
+  // find x with count(x) <= i < count(hi): the (i+1)-th smallest eigenvalue lies in [lo, hi)
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (hi - lo <= 2 * kEps * fmax(fabs(lo), fabs(hi)) + pivmin || mid == lo || mid == hi) break;
+    if (sturm_count(d, e2, n, mid, pivmin) > i)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  w[i] = 0.5 * (lo + hi);
+}
+
+// ------------------------------------------------------------ inverse iteration
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Clusters: consecutive eigenvalues closer than ortol start a shared cluster.
+__global__ void tri_clusters_kernel(const double* w, int n, const double* bounds, int* cstart, int* ncl) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double nrm = fmax(fabs(bounds[0]), fabs(bounds[1]));
+  const double ortol = 1e-3 * nrm;
+  int c = 0;
+  cstart[c++] = 0;
+  for (int i = 1; i < n; ++i)
+    if (w[i] - w[i - 1] > ortol) cstart[c++] = i;
+  cstart[c] = n;
+  *ncl = c;
+}
+
+// One thread per cluster; work: 5n doubles per thread (D, DU, DU2, DL, x) + n ints
+__global__ void tri_inviter_kernel(const double* d, const double* e, int n, const double* w, const int* cstart,
+                                   const int* ncl, const double* bounds, double* Z, int ldz, double* work,
+                                   int* iwork) {
+  const int cl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cl >= *ncl) return;
+  const double nrm = fmax(fmax(fabs(bounds[0]), fabs(bounds[1])), 1e-300);
+  const double tiny = kEps * nrm;
+  double* D = work + size_t(cl) * 5 * n;
+  double* DU = D + n;
+  double* DU2 = DU + n;
+  double* DL = DU2 + n;
+  double* x = DL + n;
+  int* piv = iwork + size_t(cl) * n;
+  const int i0 = cstart[cl], i1 = cstart[cl + 1];
+  for (int i = i0; i < i1; ++i) {
+    // perturb members of a cluster apart so the factorisations differ
+    const double lam = w[i] + (i - i0) * 10 * kEps * nrm;
+    for (int k = 0; k < n; ++k) {
+      D[k] = d[k] - lam;
+      if (k < n - 1) {
+        DU[k] = e[k];
+        DL[k] = e[k];
+      }
+      DU2[k] = 0;
+    }
+    for (int k = 0; k < n - 1; ++k) {
+      if (fabs(D[k]) >= fabs(DL[k])) {
+        if (D[k] == 0.0) D[k] = tiny;
+        const double l = DL[k] / D[k];
+        DL[k] = l;
+        D[k + 1] -= l * DU[k];
+        piv[k] = 0;
+      } else {
+        const double l = D[k] / DL[k];
+        D[k] = DL[k];
+        DL[k] = l;
+        const double t = DU[k];
+        DU[k] = D[k + 1];
+        D[k + 1] = t - l * D[k + 1];
+        if (k < n - 2) {
+          DU2[k] = DU[k + 1];
+          DU[k + 1] = -l * DU[k + 1];
+        }
+        piv[k] = 1;
+      }
+    }
+    if (D[n - 1] == 0.0) D[n - 1] = tiny;
+    for (int k = 0; k < n; ++k) x[k] = 1.0 + 0.5 * ((double)(mix64(uint64_t(i) * 1000003ull + k) >> 11) * 0x1.0p-53 - 0.5);
+    for (int itr = 0; itr < 3; ++itr) {
+      // solve (L U) y = x with the recorded row interchanges
+      for (int k = 0; k < n - 1; ++k) {
+        if (piv[k]) {
+          const double t = x[k];
+          x[k] = x[k + 1];
+          x[k + 1] = t;
+        }
+        x[k + 1] -= DL[k] * x[k];
+      }
+      x[n - 1] /= D[n - 1];
+      if (n > 1) x[n - 2] = (x[n - 2] - DU[n - 2] * x[n - 1]) / D[n - 2];
+      for (int k = n - 3; k >= 0; --k) x[k] = (x[k] - DU[k] * x[k + 1] - DU2[k] * x[k + 2]) / D[k];
+      // orthogonalise against earlier members of the cluster (MGS), normalise
+      for (int j = i0; j < i; ++j) {
+        const double* zj = Z + size_t(j) * ldz;
+        double s = 0;
+        for (int k = 0; k < n; ++k) s = fma(zj[k], x[k], s);
+        for (int k = 0; k < n; ++k) x[k] = fma(-s, zj[k], x[k]);
+      }
+      double nr = 0, mx = 0;
+      for (int k = 0; k < n; ++k) mx = fmax(mx, fabs(x[k]));
+      if (mx == 0.0) {
+        x[(i - i0) % n] = 1.0;
+        mx = 1.0;
+      }
+      for (int k = 0; k < n; ++k) {
+        x[k] /= mx;
+        nr = fma(x[k], x[k], nr);
+      }
+      nr = 1.0 / sqrt(nr);
+      for (int k = 0; k < n; ++k) x[k] *= nr;
+    }
+    double* zi = Z + size_t(i) * ldz;
+    for (int k = 0; k < n; ++k) zi[k] = x[k];
+  }
+}
+
+// ------------------------------------------------------------ QR sweeps
+// One block.  sd/se: the tridiagonal in shared memory.  Rotation r of step s
+// for shift j acts on positions (k, k+1), k = s - 3 j; recorded to rc/rs
+// [step * p + j] (c = 1, s = 0 for inactive slots).
+__global__ void tri_chase_kernel(double* d, double* e, int n, const double* sh, int p, double* rc, double* rs,
+                                 int nsteps) {
+  extern __shared__ double smem[];
+  double* sd = smem;
+  double* se = smem + n;
+  double* sx = se + n;        // carried x per shift
+  double* sz = sx + p;        // carried bulge per shift
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    sd[k] = d[k];
+    if (k < n - 1) se[k] = e[k];
+  }
+  __syncthreads();
+  for (int step = 0; step < nsteps; ++step) {
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+      const int k = step - 3 * j;
+      double c = 1.0, s = 0.0;
+      if (k >= 0 && k <= n - 2) {
+        double x, z;
+        if (k == 0) {
+          x = sd[0] - sh[j];
+          z = se[0];
+        } else {
+          x = sx[j];
+          z = sz[j];
+        }
+        const double r = hypot(x, z);
+        if (r > 0) {
+          c = x / r;
+          s = z / r;
+        }
+        if (k > 0) se[k - 1] = r;
+        const double a = sd[k], b = se[k], dd = sd[k + 1];
+        const double cs = c * s, cc = c * c, ss = s * s;
+        sd[k] = cc * a + 2 * cs * b + ss * dd;
+        sd[k + 1] = ss * a - 2 * cs * b + cc * dd;
+        se[k] = cs * (dd - a) + (cc - ss) * b;
+        if (k < n - 2) {
+          sz[j] = s * se[k + 1];
+          se[k + 1] = c * se[k + 1];
+        }
+        sx[j] = se[k];
+      }
+      rc[size_t(step) * p + j] = c;
+      rs[size_t(step) * p + j] = s;
+    }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    d[k] = sd[k];
+    if (k < n - 1) e[k] = se[k];
+  }
+}
+
+// Q (starting from I) <- Q G_1 G_2 ... ; one row of Q per thread.
+__global__ void tri_apply_rot_kernel(int n, int p, int nsteps, const double* rc, const double* rs, double* Q,
+                                     int ldq) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  for (int k = 0; k < n; ++k) Q[row + size_t(k) * ldq] = (k == row) ? 1.0 : 0.0;
+  for (int step = 0; step < nsteps; ++step) {
+    int jlo = (step - (n - 2) + 2) / 3;
+    if (jlo < 0) jlo = 0;
+    int jhi = step / 3;
+    if (jhi > p - 1) jhi = p - 1;
+    for (int j = jlo; j <= jhi; ++j) {
+      const int k = step - 3 * j;
+      if (k < 0 || k > n - 2) continue;
+      const double c = rc[size_t(step) * p + j], s = rs[size_t(step) * p + j];
+      double* q0 = Q + row + size_t(k) * ldq;
+      double* q1 = q0 + ldq;
+      const double a = *q0, b = *q1;
+      *q0 = c * a + s * b;
+      *q1 = -s * a + c * b;
+    }
+  }
+}
+
+// ------------------------------------------------------------ implicit QR (tridiagonal)
+// Symmetric tridiagonal eigen-decomposition by implicit QR steps with the
+// Wilkinson shift, deflating at the bottom (Golub and Van Loan, Alg. 8.3.2
+// and 8.3.3).  One block: thread 0 runs the scalar recurrence of one sweep
+// and records its rotations in shared memory; then every thread applies the
+// sweep to its rows of Z (Z <- Z G, full eigenvectors) when Z is given, and
+// thread 0 applies it to the row vector zl = e_{n-1}^T Z (last components,
+// the quantities of the Ritz estimate ||f|| |e_k^T y|) when zl is given.
+// On exit w holds the eigenvalues ascending and Z / zl are permuted alike.
+__global__ void tri_ql_kernel(const double* d_in, const double* e_in, int n, double* w, double* Z, int ldz,
+                              double* zl, int* status) {
+  extern __shared__ double sm[];
+  double* d = sm;
+  double* e = d + n;
+  double* rc = e + n;
+  double* rs = rc + n;
+  __shared__ int s_lo, s_hi, s_done;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    d[k] = d_in[k];
+    e[k] = (k < n - 1) ? e_in[k] : 0.0;
+  }
+  if (Z)
+    for (int64_t t = threadIdx.x; t < int64_t(n) * n; t += blockDim.x) {
+      const int i = int(t % n), j = int(t / n);
+      Z[i + size_t(j) * ldz] = (i == j) ? 1.0 : 0.0;
+    }
+  if (zl && threadIdx.x == 0)
+    for (int k = 0; k < n; ++k) zl[k] = (k == n - 1) ? 1.0 : 0.0;
+  __syncthreads();
+  int hi = n - 1, iters = 0;
+  const int max_iters = 40 * n + 100;
+  while (true) {
+    if (threadIdx.x == 0) {
+      s_done = 0;
+      // deflate converged bottom entries
+      while (hi > 0 && fabs(e[hi - 1]) <= kEps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
+        e[hi - 1] = 0.0;
+        --hi;
+      }
+      if (hi == 0 || iters >= max_iters) {
+        s_done = 1;
+        if (iters >= max_iters) atomicExch(status, (int)DEV_NOTSPD);
+      } else {
+        int lo = hi - 1;
+        while (lo > 0 && fabs(e[lo - 1]) > kEps * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
+        if (lo > 0) e[lo - 1] = 0.0;
+        const double dl = 0.5 * (d[hi - 1] - d[hi]);
+        const double eh = e[hi - 1];
+        const double den = dl + (dl >= 0 ? 1.0 : -1.0) * hypot(dl, eh);
+        const double mu = d[hi] - ((den != 0.0) ? eh * eh / den : 0.0);
+        double x = d[lo] - mu, z = e[lo];
+        for (int k = lo; k < hi; ++k) {
+          const double r = hypot(x, z);
+          double c = 1.0, s = 0.0;
+          if (r > 0.0) {
+            c = x / r;
+            s = z / r;
+          }
+          if (k > lo) e[k - 1] = r;
+          const double a = d[k], b = e[k], dd = d[k + 1];
+          const double cs = c * s, cc = c * c, ss = s * s;
+          d[k] = cc * a + 2 * cs * b + ss * dd;
+          d[k + 1] = ss * a - 2 * cs * b + cc * dd;
+          e[k] = cs * (dd - a) + (cc - ss) * b;
+          if (k < hi - 1) {
+            z = s * e[k + 1];
+            e[k + 1] = c * e[k + 1];
+          }
+          x = e[k];
+          rc[k] = c;
+          rs[k] = s;
+          if (zl) {
+            const double a0 = zl[k], b0 = zl[k + 1];
+            zl[k] = c * a0 + s * b0;
+            zl[k + 1] = -s * a0 + c * b0;
+          }
+        }
+        s_lo = lo;
+        s_hi = hi;
+        ++iters;
+      }
+    }
+    __syncthreads();
+    if (s_done) break;
+    if (Z) {
+      const int lo = s_lo, h2 = s_hi;
+      for (int row = threadIdx.x; row < n; row += blockDim.x)
+        for (int k = lo; k < h2; ++k) {
+          double* q0 = Z + row + size_t(k) * ldz;
+          double* q1 = q0 + ldz;
+          const double a0 = *q0, b0 = *q1;
+          *q0 = rc[k] * a0 + rs[k] * b0;
+          *q1 = -rs[k] * a0 + rc[k] * b0;
+        }
+    }
+    __syncthreads();
+  }
+  // sort ascending (selection sort of the values; permutation applied to Z / zl)
+  __shared__ int s_i, s_j;
+  for (int i = 0; i < n - 1; ++i) {
+    if (threadIdx.x == 0) {
+      int m = i;
+      for (int j = i + 1; j < n; ++j)
+        if (d[j] < d[m]) m = j;
+      s_i = i;
+      s_j = m;
+      if (m != i) {
+        const double t = d[i];
+        d[i] = d[m];
+        d[m] = t;
+        if (zl) {
+          const double u = zl[i];
+          zl[i] = zl[m];
+          zl[m] = u;
+        }
+      }
+    }
+    __syncthreads();
+    if (Z && s_j != s_i)
+      for (int row = threadIdx.x; row < n; row += blockDim.x) {
+        const double t = Z[row + size_t(s_i) * ldz];
+        Z[row + size_t(s_i) * ldz] = Z[row + size_t(s_j) * ldz];
+        Z[row + size_t(s_j) * ldz] = t;
+      }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < n; k += blockDim.x) w[k] = d[k];
+}
+
+// ------------------------------------------------------------ dense symmetric
+// Householder tridiagonalisation of A (n x n, lower part used), one block.
+// On exit: d, e; reflector k stored in column k of V (entries k+1..n-1) with tau[k].
+__global__ void sytrd_kernel(double* A, int lda, int n, double* d, double* e, double* tau, double* wv) {
+  __shared__ double red[32];
+  __shared__ double s_alpha, s_tau, s_scale;
+  double* v = wv;       // n
+  double* w = wv + n;   // n
+  for (int k = 0; k < n - 2; ++k) {
+    // x = A[k+1:, k]
+    double ss = 0;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) ss = fma(A[i + size_t(k) * lda], A[i + size_t(k) * lda], ss);
+    ss = block_sum(ss, red);
+    if (threadIdx.x == 0) {
+      const double x0 = A[k + 1 + size_t(k) * lda];
+      const double nx = sqrt(ss);
+      if (nx == 0.0) {
+        s_tau = 0.0;
+        s_alpha = x0;
+        s_scale = 0.0;
+      } else {
+        const double alpha = x0 >= 0 ? -nx : nx;  // new subdiagonal
+        const double v0 = x0 - alpha;
+        s_alpha = alpha;
+        s_tau = -v0 / alpha;         // H = I - tau v v^T, v[0] = 1
+        s_scale = 1.0 / v0;
+      }
+    }
+    __syncthreads();
+    const double tk = s_tau;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x)
+      v[i] = (i == k + 1) ? 1.0 : A[i + size_t(k) * lda] * s_scale;
+    __syncthreads();
+    if (tk != 0.0) {
+      // w = tau * A22 v  (A22 = A[k+1:, k+1:], symmetric, use lower triangle)
+      for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+        double s = 0;
+        for (int j = k + 1; j < n; ++j) {
+          const double aij = (i >= j) ? A[i + size_t(j) * lda] : A[j + size_t(i) * lda];
+          s = fma(aij, v[j], s);
+        }
+        w[i] = tk * s;
+      }
+      __syncthreads();
+      double vw = 0;
+      for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) vw = fma(v[i], w[i], vw);
+      vw = block_sum(vw, red);
+      const double K = -0.5 * tk * vw;
+      for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) w[i] = fma(K, v[i], w[i]);
+      __syncthreads();
+      // A22 -= v w^T + w v^T (lower triangle)
+      for (int j = k + 1; j < n; ++j)
+        for (int i = j + threadIdx.x; i < n; i += blockDim.x)
+          A[i + size_t(j) * lda] -= v[i] * w[j] + w[i] * v[j];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      d[k] = A[k + size_t(k) * lda];
+      e[k] = s_alpha;
+      tau[k] = tk;
+    }
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + size_t(k) * lda] = v[i];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (n >= 2) {
+      d[n - 2] = A[n - 2 + size_t(n - 2) * lda];
+      e[n - 2] = A[n - 1 + size_t(n - 2) * lda];
+      tau[n - 2] = 0.0;
+    }
+    d[n - 1] = A[n - 1 + size_t(n - 1) * lda];
+  }
+}
+
+// Z <- H_0 H_1 ... H_{n-3} Z, one column of Z per thread group (warp).
+__global__ void ormtr_kernel(const double* A, int lda, int n, const double* tau, double* Z, int ldz, int ncol) {
+  const int lane = threadIdx.x & 31;
+  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (col >= ncol) return;
+  double* z = Z + size_t(col) * ldz;
+  for (int k = n - 3; k >= 0; --k) {
+    const double t = tau[k];
+    if (t == 0.0) continue;
+    // v = [1, A[k+2:, k]] on rows k+1..n-1
+    double s = 0;
+    for (int i = k + 1 + lane; i < n; i += 32) s = fma((i == k + 1) ? 1.0 : A[i + size_t(k) * lda], z[i], s);
+    s = warp_sum(s) * t;
+    for (int i = k + 1 + lane; i < n; i += 32) z[i] = fma(-s, (i == k + 1) ? 1.0 : A[i + size_t(k) * lda], z[i]);
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------ Cholesky family
+__global__ void potrf_upper_kernel(double* A, int lda, int n, int* status) {
+  // A = R^T R, R upper stored in the upper triangle; one block, right-looking
+  __shared__ double piv;
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      const double a = A[j + size_t(j) * lda];
+      if (!(a > 0)) {
+        atomicExch(status, (int)DEV_NOTSPD);
+        piv = 1.0;
+      } else {
+        piv = sqrt(a);
+      }
+      A[j + size_t(j) * lda] = piv;
+    }
+    __syncthreads();
+    const double pv = piv;
+    for (int c = j + 1 + threadIdx.x; c < n; c += blockDim.x) A[j + size_t(c) * lda] /= pv;
+    __syncthreads();
+    // trailing: A[r, c] -= R[j, r] R[j, c] for j < r <= c
+    {
+      const int w = n - j - 1;
+      for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+        const int r = j + 1 + t % w, c = j + 1 + t / w;
+        if (r <= c) A[r + size_t(c) * lda] -= A[j + size_t(r) * lda] * A[j + size_t(c) * lda];
+      }
+    }
+    __syncthreads();
+  }
+  for (int c = threadIdx.x; c < n; c += blockDim.x)
+    for (int r = c + 1; r < n; ++r) A[r + size_t(c) * lda] = 0.0;
+}
+
+// Rinv = R^{-1} (upper), one thread per column
+__global__ void trinv_upper_kernel(const double* R, int ldr, int n, double* X, int ldx) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double* x = X + size_t(j) * ldx;
+  for (int i = n - 1; i >= 0; --i) {
+    if (i > j) {
+      x[i] = 0.0;
+      continue;
+    }
+    double s = (i == j) ? 1.0 : 0.0;
+    for (int k = i + 1; k <= j; ++k) s -= R[i + size_t(k) * ldr] * x[k];
+    x[i] = s / R[i + size_t(i) * ldr];
+  }
+}
+
+__global__ void potrf_lower_kernel(double* A, int lda, int n, int* status) {
+  __shared__ double piv;
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      const double a = A[j + size_t(j) * lda];
+      if (!(a > 0)) {
+        atomicExch(status, (int)DEV_NOTSPD);
+        piv = 1.0;
+      } else {
+        piv = sqrt(a);
+      }
+      A[j + size_t(j) * lda] = piv;
+    }
+    __syncthreads();
+    const double pv = piv;
+    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) A[r + size_t(j) * lda] /= pv;
+    __syncthreads();
+    {
+      const int w = n - j - 1;
+      for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+        const int r = j + 1 + t % w, c = j + 1 + t / w;
+        if (r >= c) A[r + size_t(c) * lda] -= A[r + size_t(j) * lda] * A[c + size_t(j) * lda];
+      }
+    }
+    __syncthreads();
+  }
+  for (int c = threadIdx.x; c < n; c += blockDim.x)
+    for (int r = 0; r < c; ++r) A[r + size_t(c) * lda] = 0.0;
+}
+
+__global__ void trsm_llnn_kernel(const double* L, int ldl, int n, double* B, int ldb, int nrhs) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nrhs) return;
+  double* b = B + size_t(c) * ldb;
+  for (int i = 0; i < n; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= L[i + size_t(k) * ldl] * b[k];
+    b[i] = s / L[i + size_t(i) * ldl];
+  }
+}
+__global__ void trsm_lltn_kernel(const double* L, int ldl, int n, double* B, int ldb, int nrhs) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nrhs) return;
+  double* b = B + size_t(c) * ldb;
+  for (int i = n - 1; i >= 0; --i) {
+    double s = b[i];
+    for (int k = i + 1; k < n; ++k) s -= L[k + size_t(i) * ldl] * b[k];
+    b[i] = s / L[i + size_t(i) * ldl];
+  }
+}
+
+__global__ void transpose_kernel(const double* A, int lda, int n, double* B, int ldb) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < int64_t(n) * n;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int i = int(t % n), j = int(t / n);
+    B[j + size_t(i) * ldb] = A[i + size_t(j) * lda];
+  }
+}
+__global__ void symmetrise_kernel(double* A, int lda, int n) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < int64_t(n) * n;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int i = int(t % n), j = int(t / n);
+    if (i > j) {
+      const double v = 0.5 * (A[i + size_t(j) * lda] + A[j + size_t(i) * lda]);
+      A[i + size_t(j) * lda] = v;
+      A[j + size_t(i) * lda] = v;
+    }
+  }
+}
+__global__ void csr_dense_kernel(const int32_t* rp, const int32_t* ci, const double* va, int n, double* D, int ldd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int k = 0; k < n; ++k) D[i + size_t(k) * ldd] = 0.0;
+  for (int32_t k = rp[i]; k < rp[i + 1]; ++k) D[i + size_t(ci[k]) * ldd] = va[k];
+}
+__global__ void identity_kernel(double* Q, int ldq, int n) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < int64_t(n) * n;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int i = int(t % n), j = int(t / n);
+    Q[i + size_t(j) * ldq] = (i == j) ? 1.0 : 0.0;
+  }
+}
+
+inline int g1(int64_t n, int t) {
+  int64_t b = (n + t - 1) / t;
+  if (b > 4096) b = 4096;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+// scratch layout owned by the caller: see Workspace (api.cu).
+struct TriScratch {
+  double* bounds;  // 4
+  double* e2;      // n
+  int* cstart;     // n + 1
+  int* ncl;        // 1
+  double* work;    // 5 n^2
+  int* iwork;      // n^2
+};
+static TriScratch g_tri = {};
+
+void set_tri_scratch(double* bounds, double* e2, int* cstart, int* ncl, double* work, int* iwork) {
+  g_tri = {bounds, e2, cstart, ncl, work, iwork};
+}
+
+void k_tri_eigvals(const double* d, const double* e, int n, double* w, cudaStream_t st) {
+  tri_bounds_kernel<<<1, 256, 0, st>>>(d, e, n, g_tri.bounds, g_tri.e2);
+  tri_bisect_kernel<<<(n + 63) / 64, 64, 0, st>>>(d, g_tri.e2, n, g_tri.bounds, w);
+}
+
+void k_tri_eigvecs(const double* d, const double* e, int n, const double* w, double* Z, int ldz, double* work,
+                   cudaStream_t st) {
+  (void)work;
+  tri_bounds_kernel<<<1, 256, 0, st>>>(d, e, n, g_tri.bounds, g_tri.e2);
+  tri_clusters_kernel<<<1, 32, 0, st>>>(w, n, g_tri.bounds, g_tri.cstart, g_tri.ncl);
+  tri_inviter_kernel<<<(n + 31) / 32, 32, 0, st>>>(d, e, n, w, g_tri.cstart, g_tri.ncl, g_tri.bounds, Z, ldz,
+                                                   g_tri.work, g_tri.iwork);
+}
+
+void k_tri_ql(const double* d, const double* e, int n, double* w, double* Z, int ldz, double* zl, int* status,
+              cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(tri_ql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  const size_t smem = sizeof(double) * 4 * size_t(n);
+  tri_ql_kernel<<<1, 256, smem, st>>>(d, e, n, w, Z, ldz, zl, status);
+}
+
+void k_tri_qr_sweeps(double* d, double* e, int n, const double* sh, int p, double* Q, int ldq, cudaStream_t st) {
+  const int nsteps = (n - 1) + 3 * (p - 1);
+  double* rc = g_tri.work;
+  double* rs = g_tri.work + size_t(nsteps) * p;
+  const size_t smem = sizeof(double) * (2 * size_t(n) + 2 * size_t(p));
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(tri_chase_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  tri_chase_kernel<<<1, 512, smem, st>>>(d, e, n, sh, p, rc, rs, nsteps);
+  tri_apply_rot_kernel<<<(n + 7) / 8, 8, 0, st>>>(n, p, nsteps, rc, rs, Q, ldq);
+}
+
+int k_syev(double* A, int lda, int n, double* w, double* Z, int ldz, double* work, int* dev_status,
+           cudaStream_t st) {
+  (void)dev_status;
+  // work: d (n), e (n), tau (n), wv (2n)
+  double* d = work;
+  double* e = d + n;
+  double* tau = e + n;
+  double* wv = tau + n;
+  if (n == 1) {
+    cudaMemcpyAsync(w, A, sizeof(double), cudaMemcpyDeviceToDevice, st);
+    identity_kernel<<<1, 32, 0, st>>>(Z, ldz, 1);
+    return 0;
+  }
+  sytrd_kernel<<<1, 1024, 0, st>>>(A, lda, n, d, e, tau, wv);
+  k_tri_eigvals(d, e, n, w, st);
+  k_tri_eigvecs(d, e, n, w, Z, ldz, nullptr, st);
+  ormtr_kernel<<<(n * 32 + 255) / 256, 256, 0, st>>>(A, lda, n, tau, Z, ldz, n);
+  return 0;
+}
+
+void k_potrf_upper(double* A, int lda, int n, int* dev_status, cudaStream_t st) {
+  potrf_upper_kernel<<<1, 1024, 0, st>>>(A, lda, n, dev_status);
+}
+void k_trinv_upper(const double* R, int ldr, int n, double* Rinv, int ldri, cudaStream_t st) {
+  trinv_upper_kernel<<<(n + 63) / 64, 64, 0, st>>>(R, ldr, n, Rinv, ldri);
+}
+void k_potrf_lower(double* A, int lda, int n, int* dev_status, cudaStream_t st) {
+  potrf_lower_kernel<<<1, 1024, 0, st>>>(A, lda, n, dev_status);
+}
+void k_trsm_llnn(const double* L, int ldl, int n, double* B, int ldb, int nrhs, cudaStream_t st) {
+  trsm_llnn_kernel<<<(nrhs + 63) / 64, 64, 0, st>>>(L, ldl, n, B, ldb, nrhs);
+}
+void k_trsm_lltn(const double* L, int ldl, int n, double* B, int ldb, int nrhs, cudaStream_t st) {
+  trsm_lltn_kernel<<<(nrhs + 63) / 64, 64, 0, st>>>(L, ldl, n, B, ldb, nrhs);
+}
+void k_transpose_sq(const double* A, int lda, int n, double* B, int ldb, cudaStream_t st) {
+  transpose_kernel<<<g1(int64_t(n) * n, 256), 256, 0, st>>>(A, lda, n, B, ldb);
+}
+void k_symmetrise(double* A, int lda, int n, cudaStream_t st) {
+  symmetrise_kernel<<<g1(int64_t(n) * n, 256), 256, 0, st>>>(A, lda, n);
+}
+void k_csr_to_dense(const int32_t* rp, const int32_t* ci, const double* va, int n, double* D, int ldd,
+                    cudaStream_t st) {
+  csr_dense_kernel<<<(n + 127) / 128, 128, 0, st>>>(rp, ci, va, n, D, ldd);
+}
+void k_set_identity(double* Q, int ldq, int n, cudaStream_t st) {
+  identity_kernel<<<g1(int64_t(n) * n, 256), 256, 0, st>>>(Q, ldq, n);
+}
+
+}  // namespace mmd

@@ -1,0 +1,116 @@
+// Launch wrappers of the library's CUDA kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dev_common.cuh"
+
+namespace mmd {
+
+struct SolverArgs {
+  int mode;  // 0 CG, 1 flexible PCG with inner CG on M, 2 CG on P A P
+  int64_t n;
+  const int32_t* arp;
+  const int32_t* acol;
+  const double* aval;
+  const int32_t* mrp;
+  const int32_t* mcol;
+  const double* mval;
+  const int32_t* seg_ptr;
+  const double* phi;
+  int64_t nseg;
+  int m;
+  int64_t ld;
+  const double* b;
+  double* x;
+  int x0;
+  double *r, *p, *q, *z;
+  double *ir, *ip, *iq;
+  double tol, itol;
+  int maxit, imaxit;
+  double* red;         // [4][MT][grid]
+  int64_t* it_out;     // [m]
+  int64_t* in_out;     // [1], accumulated
+  int* conv;           // [m]
+  GridBarrier bar;
+};
+
+int solver_threads();
+int solver_max_grid(int tpr, int mt, int num_sms);
+cudaError_t launch_solver(const SolverArgs& a, int tpr, int mt, int grid, cudaStream_t st);
+
+// ---- vector / sparse kernels (blas.cu)
+void k_fill(double* x, int64_t n, double v, cudaStream_t st);
+void k_copy(double* y, const double* x, int64_t n, cudaStream_t st);
+void k_scal(double* x, int64_t n, double a, cudaStream_t st);
+void k_scal_dev(double* x, int64_t n, const double* a, int invert, cudaStream_t st);
+void k_axpy(double* y, const double* x, int64_t n, double a, cudaStream_t st);
+// y = A x (CSR), columns m of ld (x, y column-major)
+void k_spmv(const int32_t* rp, const int32_t* ci, const double* va, int64_t nrows, const double* x, int64_t ldx,
+            double* y, int64_t ldy, int m, int tpr, cudaStream_t st);
+// dot products: out[c] = sum_i x(i,c) y(i,c), deterministic two-stage; scratch >= 1024*m doubles
+void k_dots(const double* x, const double* y, int64_t n, int64_t ld, int m, double* out, double* scratch,
+            cudaStream_t st);
+// h = B^T u (B: n x j col-major, ldb) deterministic; scratch >= chunks*j
+void k_gemv_t(const double* B, int64_t ldb, int64_t n, int j, const double* u, double* h, double* scratch,
+              cudaStream_t st);
+// y += alpha * B h  (B: n x j)
+void k_gemv_n(const double* B, int64_t ldb, int64_t n, int j, const double* h, double alpha, double* y,
+              cudaStream_t st);
+// C (m x n, ldc) = alpha A^T B + beta C, A: K x m (lda), B: K x n (ldb); deterministic split-K
+void k_gemm_tn(int m, int n, int64_t K, double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+               double beta, double* C, int64_t ldc, double* scratch, int64_t scratch_len, cudaStream_t st);
+// C (M x n, ldc) = alpha A B + beta C, A: M x k (lda), B: k x n (ldb); M long
+void k_gemm_nn(int64_t M, int n, int k, double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+               double beta, double* C, int64_t ldc, cudaStream_t st);
+// gather / scatter by permutation: y[i] = x[perm[i]] (columns m, ld)
+void k_gather(const double* x, int64_t ldx, const int32_t* perm, int64_t n, int m, double* y, int64_t ldy,
+              cudaStream_t st);
+void k_scatter(const double* x, int64_t ldx, const int32_t* perm, int64_t n, int m, double* y, int64_t ldy,
+               cudaStream_t st);
+// project each column onto range(P): x -= phi (phi^T x) per segment
+void k_project(double* x, int64_t ld, int m, const int32_t* seg_ptr, const double* phi, int64_t nseg,
+               cudaStream_t st);
+// columns: x(:,c) *= s[c]
+void k_scale_cols(double* x, int64_t ld, int64_t n, int m, const double* s, cudaStream_t st);
+// SplitMix64 counter random vector in [-1, 1)
+void k_random(double* x, int64_t n, uint64_t seed, uint64_t stream, const int32_t* perm, cudaStream_t st);
+// column norms^2: out[c] = sum x(:,c)^2
+// sign fix + normalise columns (largest |.| positive, ties lowest index)
+void k_normalise_sign(double* V, int64_t ld, int64_t n, int m, double* scratch, cudaStream_t st);
+// residual norms ||A v - l v||: out[c]
+void k_residuals(const int32_t* rp, const int32_t* ci, const double* va, int64_t n, const double* V, int64_t ld,
+                 int m, const double* lam, double* out, double* scratch, cudaStream_t st);
+
+// ---- small dense (dense.cu); all matrices column-major
+// eigenvalues of symmetric tridiagonal (d: n, e: n-1) by bisection, ascending
+void k_tri_eigvals(const double* d, const double* e, int n, double* w, cudaStream_t st);
+// eigenvectors of symmetric tridiagonal for eigenvalues w (ascending), Z: n x n (ldz)
+void k_tri_eigvecs(const double* d, const double* e, int n, const double* w, double* Z, int ldz, double* work,
+                   cudaStream_t st);
+// implicit-QR eigen-decomposition of a symmetric tridiagonal (n <= 6000):
+// w ascending; Z (n x n) full eigenvectors if non-NULL; zl (n) last row of Z if non-NULL
+void k_tri_ql(const double* d, const double* e, int n, double* w, double* Z, int ldz, double* zl, int* status,
+              cudaStream_t st);
+// p shifted implicit QR sweeps on tridiagonal (d, e) of order n with shifts sh[0..p-1];
+// Q (n x n) is overwritten with the accumulated orthogonal factor (starting from I).
+void k_tri_qr_sweeps(double* d, double* e, int n, const double* sh, int p, double* Q, int ldq, cudaStream_t st);
+// dense symmetric eig: A (n x n) -> w ascending, Z eigenvectors (may alias A). work: >= 4 n^2 + 8 n doubles
+int k_syev(double* A, int lda, int n, double* w, double* Z, int ldz, double* work, int* dev_status,
+           cudaStream_t st);
+// Cholesky A = R^T R (upper R in place), status set on failure; Rinv = R^{-1} upper
+void k_potrf_upper(double* A, int lda, int n, int* dev_status, cudaStream_t st);
+void k_trinv_upper(const double* R, int ldr, int n, double* Rinv, int ldri, cudaStream_t st);
+// lower Cholesky L (in place), and C = L^{-1} A L^{-T} for the generalized problem
+void k_potrf_lower(double* A, int lda, int n, int* dev_status, cudaStream_t st);
+void k_trsm_llnn(const double* L, int ldl, int n, double* B, int ldb, int nrhs, cudaStream_t st);  // B = L^{-1} B
+void k_trsm_lltn(const double* L, int ldl, int n, double* B, int ldb, int nrhs, cudaStream_t st);  // B = L^{-T} B
+void k_transpose_sq(const double* A, int lda, int n, double* B, int ldb, cudaStream_t st);
+void k_symmetrise(double* A, int lda, int n, cudaStream_t st);
+void k_csr_to_dense(const int32_t* rp, const int32_t* ci, const double* va, int n, double* D, int ldd,
+                    cudaStream_t st);
+// tridiagonal (alpha, beta) -> dense-free utilities
+void k_set_identity(double* Q, int ldq, int n, cudaStream_t st);
+
+}  // namespace mmd

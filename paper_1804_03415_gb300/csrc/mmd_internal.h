@@ -1,0 +1,83 @@
+// Internal structures of the mmdeig library (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mmdeig.h"
+
+namespace mmd {
+
+// Host CSR matrix (int32 indices, sorted columns).
+struct HCSR {
+  int64_t nrows = 0, ncols = 0;
+  std::vector<int32_t> rowptr, col;
+  std::vector<double> val;
+  int64_t nnz() const { return rowptr.empty() ? 0 : rowptr.back(); }
+};
+
+// One level k >= 1 of the decomposition in natural (build) order.
+struct HLevel {
+  int64_t n_fine = 0, n = 0;
+  std::vector<int32_t> patch_of, patch_ptr, patch_rows, omega_ptr, omega_rows;
+  std::vector<double> phi, uhat;
+  HCSR psi;  // n_fine x n
+  HCSR A, M;
+  double eps = 0, delta = 0;
+  int used_closed = 0;
+};
+
+// Device CSR (device order).
+struct DCSR {
+  int64_t nrows = 0, ncols = 0, nnz = 0;
+  int32_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  float* val32 = nullptr;
+  double mean_row = 0;
+  int max_row = 0;
+};
+
+// Device level data.  Level k's vectors are stored in "device order": the
+// rows of level k sorted by the patches of level k + 1 (patch by patch, so
+// each patch of level k + 1 is a contiguous segment); the coarsest level keeps
+// its natural order.
+struct DLevel {
+  int64_t n = 0;
+  DCSR A;          // A^(k)
+  DCSR M;          // M^(k), k >= 1
+  DCSR psi;        // Psi^(k): level k-1 (rows) x level k (cols), k >= 1
+  // patches of level k+1 over this level's rows (k < K): contiguous segments
+  int64_t nseg = 0;
+  int32_t* seg_ptr = nullptr;  // nseg + 1
+  double* phi_next = nullptr;  // phi^(k+1) per row of this level (device order)
+  std::vector<int32_t> perm;   // device position -> natural index (host copy)
+  int32_t* d_perm = nullptr;   // same on device
+  int32_t* d_iperm = nullptr;  // natural index -> device position
+  double eps = 0, delta = 0;   // of P^(k) (k >= 1)
+};
+
+struct Workspace;
+
+}  // namespace mmd
+
+struct mmd_handle {
+  mmd::HCSR A0;                      // input, natural order
+  std::vector<mmd::HLevel> levels;   // k = 1..K at index k-1
+  mmd_build_opts bopts;
+  bool on_device = false;
+  int device = -1;
+  std::vector<mmd::DLevel> dl;       // k = 0..K
+  mmd::Workspace* ws = nullptr;
+  double normA_inf = 0;
+};
+
+namespace mmd {
+
+void set_error(const std::string& msg);
+int build_host(const mmd_csr* A, const mmd_build_opts* o, mmd_handle* h);
+int upload_levels(mmd_handle* h);
+void free_device(mmd_handle* h);
+
+}  // namespace mmd

@@ -1,0 +1,87 @@
+"""C ABI on the CPU: the library loads, exports every declared entry point,
+and its host-only decomposition build is bit-exact with the oracle's integer
+indexing (patches, supports, symbolic patterns) and matches its floats."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mmd as OM
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1804_03415_gb300 import build as B
+
+    B.build()
+    import paper_1804_03415_gb300 as P
+
+    P._lib.load()
+    return P
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "mmdeig.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:int|int64_t|void|const char\*)\s+\**\s*(\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(pkg):
+    names = declared_functions()
+    assert len(names) >= 12
+    lib = ctypes.CDLL(pkg._lib.LIB_PATH)
+    for nm in names:
+        assert hasattr(lib, nm), nm
+    assert set(names) <= set(pkg._lib.SIGNATURES), set(names) - set(pkg._lib.SIGNATURES)
+
+
+def test_strerror_and_validation(pkg):
+    lib = pkg._lib.load()
+    assert lib.mmd_strerror(0) == b"ok"
+    assert lib.mmd_strerror(-3).startswith(b"iteration")
+    # malformed CSR: unsorted columns, asymmetric values, missing diagonal
+    A = W.fd2d(4, const=True)
+    bad = A.col.copy()
+    bad[[1, 2]] = bad[[2, 1]]
+    with pytest.raises(pkg.MMDError):
+        pkg.MMD(A.rowptr, bad, A.val, device=False)
+    v = A.val.copy()
+    v[1] += 0.5
+    with pytest.raises(pkg.MMDError):
+        pkg.MMD(A.rowptr, A.col, v, device=False)
+    # a row without its diagonal
+    rp, ci, va = A.rowptr.copy(), A.col.copy(), A.val.copy()
+    i0 = np.where(ci[rp[0]:rp[1]] == 0)[0][0]
+    keep = np.ones(len(ci), bool)
+    keep[rp[0] + i0] = False
+    rp2 = rp.copy()
+    rp2[1:] -= 1
+    with pytest.raises(pkg.MMDError):
+        pkg.MMD(rp2, ci[keep], va[keep], device=False)
+
+
+@pytest.mark.parametrize("case", ["fd2d_32", "torus_4000", "rgg_3000"])
+def test_host_build_matches_oracle(pkg, case):
+    A = {"fd2d_32": lambda: W.fd2d(32, seed=3), "torus_4000": lambda: W.torus_knn(4000, seed=4),
+         "rgg_3000": lambda: W.rgg(3000, seed=5)}[case]()
+    h = pkg.MMD(A.rowptr, A.col, A.val, device=False, n_coarse=50)
+    D = OM.build(A, OM.BuildOpts(n_coarse=50))
+    assert h.num_levels == D.K
+    for k in range(1, D.K + 1):
+        L, O = h.level(k), D.levels[k - 1]
+        for f in ["patch_of", "patch_ptr", "patch_rows", "omega_ptr", "omega_rows"]:
+            assert np.array_equal(L[f], getattr(O, f)), (k, f)
+        for nm, mat in [("A", O.A), ("M", O.M), ("psi", O.psi)]:
+            rp, ci, va = L[nm]
+            assert np.array_equal(rp, mat.indptr) and np.array_equal(ci, mat.indices), (k, nm)
+            assert np.abs(va - mat.data).max() <= 1e-10 * np.abs(mat.data).max(), (k, nm)
+        assert abs(L["eps"] - O.eps) <= 1e-10 * O.eps
+        assert abs(L["delta"] - O.delta) <= 1e-10 * O.delta
+        assert L["used_closed"] == O.used_closed
+    h.close()

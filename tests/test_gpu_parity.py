@@ -1,0 +1,200 @@
+"""CUDA path against the CPU oracle, element by element, through the C ABI.
+
+Tolerances (floating point, FP64 path):
+  * level matrices and SpMV: 1e-12 relative (same products, different
+    summation order);
+  * OP / B-solve outputs: both sides stop at relative residual eps, so each
+    is within cond * eps of the exact solution; they are compared with the
+    exact dense solution at a tolerance derived from eps;
+  * eigenvalues: relative error <= 1e-9, and eigenvectors compared as
+    subspaces of clusters (relative gap < 1e-6): every principal angle
+    cosine >= 1 - 1e-12 (angle <= ~1.4e-6);
+  * integer level/patch indexing: bit-exact.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import eig as OE
+from oracle import mmd as OM
+from oracle import solvers as OS
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _pkg():
+    import paper_1804_03415_gb300 as pkg
+
+    return pkg
+
+
+def _handle(A, **kw):
+    pkg = _pkg()
+    return pkg.MMD(A.rowptr, A.col, A.val, **kw)
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def clusters(lam, rel=1e-6):
+    out, cur = [], [0]
+    for i in range(1, len(lam)):
+        if abs(lam[i] - lam[i - 1]) <= rel * max(abs(lam[i]), abs(lam[i - 1])):
+            cur.append(i)
+        else:
+            out.append(cur)
+            cur = [i]
+    out.append(cur)
+    return out
+
+
+def assert_eigpairs_match(lam, V, lam_ref, V_ref, rtol=1e-9, cos_tol=1e-12):
+    rel = np.abs(lam - lam_ref) / np.abs(lam_ref)
+    assert rel.max() <= rtol, f"eigenvalue rel err {rel.max():.3e}"
+    for cl in clusters(lam_ref):
+        if cl[-1] == len(lam_ref) - 1 and len(cl) > 1:
+            continue  # a cluster cut by N: only the span of the whole cluster is unique
+        s = np.linalg.svd(V[:, cl].T @ V_ref[:, cl], compute_uv=False)
+        assert s.min() >= 1 - cos_tol, f"subspace of cluster {cl}: min cos {s.min():.16f}"
+
+
+@pytest.fixture(scope="module")
+def fd_case():
+    A = W.fd2d(32, seed=W.BASE_SEED + 7)
+    return A, OM.build(A, OM.BuildOpts(n_coarse=60))
+
+
+def test_build_bitexact_and_levels(fd_case):
+    A, D = fd_case
+    h = _handle(A, n_coarse=60)
+    assert h.num_levels == D.K
+    for k in range(1, D.K + 1):
+        L, O = h.level(k), D.levels[k - 1]
+        for f in ["patch_of", "patch_ptr", "patch_rows", "omega_ptr", "omega_rows"]:
+            assert np.array_equal(L[f], getattr(O, f)), f
+        for nm, mat in [("A", O.A), ("M", O.M), ("psi", O.psi)]:
+            rp, ci, va = L[nm]
+            assert np.array_equal(rp, mat.indptr) and np.array_equal(ci, mat.indices), nm
+            assert np.abs(va - mat.data).max() <= 1e-10 * np.abs(mat.data).max(), nm
+    h.close()
+
+
+def test_level_spmv(fd_case):
+    A, D = fd_case
+    h = _handle(A, n_coarse=60)
+    rng = np.random.default_rng(1)
+    for k in range(0, D.K + 1):
+        n = D.N(k)
+        x = rng.standard_normal(n)
+        for which in ([0] if k == 0 else [0, 1]):
+            y = torch.zeros(n, dtype=torch.float64, device="cuda")
+            h.level_spmv(k, which, _dev(x), y)
+            M = D.A(k) if which == 0 else D.M(k)
+            ref = M @ x
+            assert np.abs(y.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    h.close()
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_level_op_matches_oracle(fd_case, k):
+    A, D = fd_case
+    if k > D.K:
+        pytest.skip("level absent")
+    h = _handle(A, n_coarse=60)
+    n = D.N(k)
+    x = np.random.default_rng(k).standard_normal(n)
+    tol = 1e-12
+    y = torch.zeros(n, dtype=torch.float64, device="cuda")
+    it = h.level_op(k, _dev(x), y, tol)
+    ctr = OS.Counters()
+    yo = OS.op(D.A(k), D.M(k), x, tol, ctr=ctr)
+    Ad = D.A(k).toarray()
+    rhs = x if k == 0 else D.M(k) @ x
+    exact = np.linalg.solve(Ad, rhs)
+    cond = np.linalg.cond(Ad)
+    bound = 10 * cond * tol * np.linalg.norm(exact)
+    yg = y.cpu().numpy()
+    assert np.linalg.norm(yg - exact) <= bound
+    assert np.linalg.norm(yo - exact) <= bound
+    # same algorithm: iteration counts agree closely (rounding may move the stop by a step)
+    assert abs(it - ctr.pcg_iters) <= max(2, 0.05 * ctr.pcg_iters)
+    h.close()
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_level_bsolve_matches_oracle(fd_case, k):
+    A, D = fd_case
+    if k > D.K:
+        pytest.skip("level absent")
+    h = _handle(A, n_coarse=60)
+    lev = D.levels[k - 1]
+    Af = D.A(k - 1)
+    Mf = D.M(k - 1)
+    q = np.random.default_rng(10 + k).standard_normal(lev.n_fine)
+    tol = 1e-12
+    x = torch.zeros(lev.n_fine, dtype=torch.float64, device="cuda")
+    h.level_bsolve(k, _dev(q), x, tol)
+    rhs = OM.Ut_apply(lev, q if Mf is None else Mf @ q)
+    g = OS.bsolve(Af, lev, rhs, tol)
+    xo = OM.U_apply(lev, g)
+    U = OM.U_apply(lev, np.eye(lev.n_fine - lev.n))
+    B = U.T @ Af.toarray() @ U
+    exact = U @ np.linalg.solve(B, rhs)
+    bound = 10 * np.linalg.cond(B) * tol * np.linalg.norm(exact)
+    assert np.linalg.norm(x.cpu().numpy() - exact) <= bound
+    assert np.linalg.norm(xo - exact) <= bound
+    h.close()
+
+
+EIG_CASES = {
+    "fd2d_24": (lambda: W.fd2d(24, seed=W.BASE_SEED + 11), 16, 1e-10, 50),
+    "fd2d_const_18": (lambda: W.fd2d(18, const=True), 12, 1e-10, 40),
+    "torus_3000": (lambda: W.torus_knn(3000, seed=W.BASE_SEED + 12), 24, 1e-8, 80),
+    "rgg_2500": (lambda: W.rgg(2500, deg=8.0, seed=W.BASE_SEED + 13), 16, 1e-8, 60),
+}
+
+
+@pytest.mark.parametrize("name", sorted(EIG_CASES))
+def test_eig_leftmost_matches_oracle(name):
+    make, N, tol, nc = EIG_CASES[name]
+    A = make()
+    ref = OE.eig_leftmost(OM.build(A, OM.BuildOpts(n_coarse=nc)), N, tol)
+    h = _handle(A, n_coarse=nc)
+    lam, V, st = h.eig_leftmost(N, tol)
+    assert_eigpairs_match(lam, V, ref.lam, ref.V)
+    assert st["max_rel_residual"] <= 10 * tol
+    assert np.allclose(V.T @ V, np.eye(N), atol=1e-10)
+    # also against dense brute force
+    ev = np.linalg.eigvalsh(A.dense())[:N]
+    assert np.abs(lam - ev).max() <= 1e-9 * np.abs(ev).max() + 1e-12 * ev[-1]
+    h.close()
+
+
+def test_eig_device_outputs_and_edge_cases():
+    pkg = _pkg()
+    A = W.fd2d(12, seed=W.BASE_SEED + 14)
+    h = _handle(A, n_coarse=30)
+    N = 5
+    lam = torch.zeros(N, dtype=torch.float64, device="cuda")
+    V = torch.zeros((N, A.n), dtype=torch.float64, device="cuda")
+    h.eig_leftmost(N, 1e-10, out=(lam, V))
+    ev = np.linalg.eigvalsh(A.dense())[:N]
+    assert np.allclose(lam.cpu().numpy(), ev, rtol=1e-9)
+    # N out of range, bad tol
+    with pytest.raises(pkg.MMDError):
+        h.eig_leftmost(0, 1e-8)
+    with pytest.raises(pkg.MMDError):
+        h.eig_leftmost(A.n + 1, 1e-8)
+    with pytest.raises(pkg.MMDError):
+        h.eig_leftmost(3, -1.0)
+    h.close()
+    # a matrix small enough to have no coarse level: dense solve at level 0
+    B = W.fd2d(6, seed=W.BASE_SEED + 15)
+    h = _handle(B, n_coarse=300)
+    assert h.num_levels == 0
+    lam, V, st = h.eig_leftmost(36, 1e-10)
+    assert np.allclose(lam, np.linalg.eigvalsh(B.dense()), rtol=1e-9)
+    h.close()
