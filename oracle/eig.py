@@ -27,7 +27,13 @@ notes of the repository):
 * Implicit restart (Algorithm 2): exact shifts = the p smallest Ritz values
   of T_{k+p} computed after the p-step extension; f update uses the
   pre-truncation basis.
-* "c . d steps of shifts" (Algorithm 4): p = c_r d with c_r = 1.
+* "c . d steps of shifts" (Algorithm 4): p = max(c_r d, k) with c_r = 1, k the
+  current dimension (the factorisation doubles before the shifts, as in ARPACK;
+  with the paper's d = N/10 a single shift per restart stalls for small N).
+* Refinement window (Algorithm 5, renew m_h): besides mu_mh >= mu_re, keep
+  mu_mh >= mu_ml alpha / (1 + beta), the ratio of the efficiency condition (ii)
+  of Section 6, so the first m_h columns converge even when the coarser level
+  stopped on the pair count instead of mu_ex.
 * Lanczos residual: max over all Ritz pairs of T of ||f||_M |e_k^T y_i|.
 * M-QR in Algorithm 5: column-scaled CholQR2 in the M inner product.
 * S = W^T F is symmetrised before its eigen-decomposition (descending).
@@ -194,7 +200,7 @@ def extend(A, M, Vini, Dini, pcg_tol, res_ok, mu_ex, d, m_tar, opts: EigOpts, ct
             th, _, res = lz.ritz()
             if res_ok(th, res):
                 return
-            pp_eff = min(pp, room - lz.j)
+            pp_eff = min(max(pp, lz.j), room - lz.j)
             if pp_eff <= 0:
                 return
             k = lz.j
@@ -268,7 +274,9 @@ def refine(Ah, Mh, lev_l: _mmd.Level, Q0, D0, tol_rel, mu_re, eps_h, delta_h, op
         D, P = np.linalg.eigh(S)
         order = np.argsort(-D, kind="stable")
         D, P = D[order], P[:, order]
-        mh = int(np.sum(D >= mu_re))
+        # renew m_h (keep mu_mh >= mu_re); keep a spectral gap to the end of the
+        # window, mu_mh >= mu_ml * alpha / (1 + beta) (efficiency condition (ii), Section 6)
+        mh = int(np.sum(D >= max(mu_re, D[-1] * opts.alpha / (1.0 + opts.beta))))
         Q = Q @ P
         F = F @ P
         st.refine_iters = it

@@ -98,6 +98,61 @@ static int upload_csr(const HCSR& A, DCSR& D) {
   int mx = 0;
   for (int64_t i = 0; i < A.nrows; ++i) mx = std::max(mx, A.rowptr[i + 1] - A.rowptr[i]);
   D.max_row = mx;
+  // SELL-32: rows sorted by length (descending, stable) inside windows of 256,
+  // slices of 32 rows stored column-major, padded with zeros (column = row).
+  const int64_t n = A.nrows, ns = (n + 31) / 32;
+  std::vector<int32_t> order(n);
+  for (int64_t i = 0; i < n; ++i) order[i] = (int32_t)i;
+  for (int64_t w0 = 0; w0 < n; w0 += 256) {
+    const int64_t w1 = std::min<int64_t>(n, w0 + 256);
+    std::stable_sort(order.begin() + w0, order.begin() + w1, [&](int32_t a, int32_t b) {
+      return (A.rowptr[a + 1] - A.rowptr[a]) > (A.rowptr[b + 1] - A.rowptr[b]);
+    });
+  }
+  std::vector<int32_t> sptr(ns + 1, 0), slen(ns, 0), srow(ns * 32, -1);
+  for (int64_t s = 0; s < ns; ++s) {
+    int w = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int64_t t = s * 32 + l;
+      if (t < n) {
+        srow[t] = order[t];
+        w = std::max(w, A.rowptr[order[t] + 1] - A.rowptr[order[t]]);
+      }
+    }
+    slen[s] = w;
+    if (int64_t(sptr[s]) + int64_t(w) * 32 >= (int64_t(1) << 31)) {
+      set_error("SELL copy exceeds 2^31 entries");
+      return MMD_EINVAL;
+    }
+    sptr[s + 1] = sptr[s] + w * 32;
+  }
+  const int64_t tot = sptr[ns];
+  std::vector<int32_t> scol(tot);
+  std::vector<double> sval(tot, 0.0);
+  for (int64_t s = 0; s < ns; ++s)
+    for (int l = 0; l < 32; ++l) {
+      const int32_t r = srow[s * 32 + l];
+      const int32_t k0 = r >= 0 ? A.rowptr[r] : 0, len = r >= 0 ? A.rowptr[r + 1] - k0 : 0;
+      for (int k = 0; k < slen[s]; ++k) {
+        const int64_t o = sptr[s] + int64_t(k) * 32 + l;
+        if (k < len) {
+          scol[o] = A.col[k0 + k];
+          sval[o] = A.val[k0 + k];
+        } else {
+          scol[o] = r >= 0 ? std::min<int32_t>(r, (int32_t)A.ncols - 1) : 0;
+          sval[o] = 0.0;
+        }
+      }
+    }
+  D.nslices = ns;
+  D.sell_nnz = tot;
+  if ((rc = dput(&D.s_ptr, sptr))) return rc;
+  if ((rc = dput(&D.s_len, slen))) return rc;
+  if ((rc = dput(&D.s_row, srow))) return rc;
+  if ((rc = dput(&D.s_col, scol))) return rc;
+  if ((rc = dput(&D.s_val, sval))) return rc;
+  std::vector<float> sv32(sval.begin(), sval.end());
+  if ((rc = dput(&D.s_val32, sv32))) return rc;
   return MMD_OK;
 }
 
@@ -106,6 +161,12 @@ static void free_csr(DCSR& D) {
   cudaFree(D.col);
   cudaFree(D.val);
   cudaFree(D.val32);
+  cudaFree(D.s_ptr);
+  cudaFree(D.s_len);
+  cudaFree(D.s_row);
+  cudaFree(D.s_col);
+  cudaFree(D.s_val);
+  cudaFree(D.s_val32);
   D = DCSR();
 }
 

@@ -40,32 +40,30 @@ __global__ void axpy_kernel(double* y, const double* x, int64_t n, double a) {
     y[i] = fma(a, x[i], y[i]);
 }
 
-template <int TPR>
-__global__ void spmv_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                            const double* __restrict__ va, int64_t n, const double* __restrict__ x, int64_t ldx,
-                            double* __restrict__ y, int64_t ldy, int m) {
-  const int lane = threadIdx.x % TPR;
-  const int64_t g = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / TPR;
-  const int64_t Gs = (int64_t(gridDim.x) * blockDim.x) / TPR;
+// y = A x, SELL-32: one warp per slice of 32 rows, one row per lane, one FMA
+// per stored entry (FP64 instructions are scarce on GB300); up to 4 columns
+// per pass so a matrix entry is loaded once for 4 right-hand sides.
+__global__ void spmv_kernel(Sell A, const double* __restrict__ x, int64_t ldx, double* __restrict__ y,
+                            int64_t ldy, int m) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int c0 = 0; c0 < m; c0 += 4) {
     const int mc = (m - c0) < 4 ? (m - c0) : 4;
-    for (int64_t base = 0;; base += Gs) {
-      const int64_t i = g + base;
-      if (!__any_sync(0xffffffffu, i < n)) break;
+    for (int64_t sl = gw; sl < A.nslices; sl += nw) {
+      const int32_t base = A.ptr[sl], len = A.len[sl];
+      const int32_t row = A.row[sl * 32 + lane];
       double acc[4] = {0, 0, 0, 0};
-      if (i < n) {
-        for (int32_t k = rp[i] + lane; k < rp[i + 1]; k += TPR) {
-          const double a = va[k];
-          const int64_t j = ci[k];
+      for (int32_t k = 0; k < len; ++k) {
+        const int32_t o = base + k * 32 + lane;
+        const double a = A.val[o];
+        const int64_t j = A.col[o];
 #pragma unroll
-          for (int c = 0; c < 4; ++c)
-            if (c < mc) acc[c] = fma(a, x[j + (c0 + c) * ldx], acc[c]);
-        }
+        for (int c = 0; c < 4; ++c)
+          if (c < mc) acc[c] = fma(a, x[j + (c0 + c) * ldx], acc[c]);
       }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[c] = group_sum<TPR>(acc[c]);
-      if (i < n && lane == 0)
-        for (int c = 0; c < mc; ++c) y[i + (c0 + c) * ldy] = acc[c];
+      if (row >= 0)
+        for (int c = 0; c < mc; ++c) y[row + (c0 + c) * ldy] = acc[c];
     }
   }
 }
@@ -339,6 +337,29 @@ __global__ void sqrt_kernel(double* x, int m) {
 
 }  // namespace
 
+__global__ void sub_kernel(double* r, const double* b, const double* y, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    r[i] = b[i] - y[i];
+}
+__global__ void to_f32_kernel(float* f, const double* d, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    f[i] = (float)d[i];
+}
+__global__ void add_f32_kernel(double* x, const float* f, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    x[i] += (double)f[i];
+}
+
+void k_sub(double* r, const double* b, const double* y, int64_t n, cudaStream_t st) {
+  sub_kernel<<<nblk(n, 256), 256, 0, st>>>(r, b, y, n);
+}
+void k_to_f32(float* f, const double* d, int64_t n, cudaStream_t st) {
+  to_f32_kernel<<<nblk(n, 256), 256, 0, st>>>(f, d, n);
+}
+void k_add_f32(double* x, const float* f, int64_t n, cudaStream_t st) {
+  add_f32_kernel<<<nblk(n, 256), 256, 0, st>>>(x, f, n);
+}
+
 void k_fill(double* x, int64_t n, double v, cudaStream_t st) { fill_kernel<<<nblk(n, 256), 256, 0, st>>>(x, n, v); }
 void k_copy(double* y, const double* x, int64_t n, cudaStream_t st) {
   copy_kernel<<<nblk(n, 256), 256, 0, st>>>(y, x, n);
@@ -351,19 +372,12 @@ void k_axpy(double* y, const double* x, int64_t n, double a, cudaStream_t st) {
   axpy_kernel<<<nblk(n, 256), 256, 0, st>>>(y, x, n, a);
 }
 
-void k_spmv(const int32_t* rp, const int32_t* ci, const double* va, int64_t nrows, const double* x, int64_t ldx,
-            double* y, int64_t ldy, int m, int tpr, cudaStream_t st) {
-  const int64_t groups = nrows;
+void k_spmv(const Sell& A, const double* x, int64_t ldx, double* y, int64_t ldy, int m, cudaStream_t st) {
   const int threads = 256;
-  int64_t blocks = (groups * tpr + threads - 1) / threads;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  int64_t blocks = (A.nslices * 32 + threads - 1) / threads;
+  if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks < 1) blocks = 1;
-  if (tpr <= 4)
-    spmv_kernel<4><<<(int)blocks, threads, 0, st>>>(rp, ci, va, nrows, x, ldx, y, ldy, m);
-  else if (tpr <= 8)
-    spmv_kernel<8><<<(int)blocks, threads, 0, st>>>(rp, ci, va, nrows, x, ldx, y, ldy, m);
-  else
-    spmv_kernel<32><<<(int)blocks, threads, 0, st>>>(rp, ci, va, nrows, x, ldx, y, ldy, m);
+  spmv_kernel<<<(int)blocks, threads, 0, st>>>(A, x, ldx, y, ldy, m);
 }
 
 void k_dots(const double* x, const double* y, int64_t n, int64_t ld, int m, double* out, double* scratch,
@@ -440,12 +454,12 @@ void k_normalise_sign(double* V, int64_t ld, int64_t n, int m, double* scratch, 
   (void)scratch;
   if (m > 0) normalise_sign_kernel<<<m, 1024, 0, st>>>(V, ld, n);
 }
-void k_residuals(const int32_t* rp, const int32_t* ci, const double* va, int64_t n, const double* V, int64_t ld,
-                 int m, const double* lam, double* out, double* scratch, cudaStream_t st) {
+void k_residuals(const Sell& A, int64_t n, const double* V, int64_t ld, int m, const double* lam, double* out,
+                 double* scratch, cudaStream_t st) {
   // scratch: n*m (A V) + 512*m partials
   double* Y = scratch;
   double* part = scratch + n * m;
-  k_spmv(rp, ci, va, n, V, ld, Y, n, m, 8, st);
+  k_spmv(A, V, ld, Y, n, m, st);
   int nb = (int)((n + 255) / 256);
   if (nb > kDotBlocks) nb = kDotBlocks;
   resid_stage1<<<nb, 256, 0, st>>>(Y, V, ld, n, m, lam, part);

@@ -407,6 +407,112 @@ __global__ void tri_ql_kernel(const double* d_in, const double* e_in, int n, dou
   for (int k = threadIdx.x; k < n; k += blockDim.x) w[k] = d[k];
 }
 
+// ------------------------------------------------------------ parallel Jacobi
+// Two-sided cyclic Jacobi on a symmetric matrix (Golub and Van Loan, Section
+// 8.5; parallel round-robin ordering, Section 8.5.5).  Jacobi keeps relative
+// accuracy on graded matrices (Demmel and Veselic 1992), which the Rayleigh-
+// Ritz matrices of the refinement are: nearly diagonal with Ritz values that
+// span many orders of magnitude.  Cooperative launch; every round:
+//   phase 1: one thread per pair (p, q) computes its rotation (c, s);
+//   phase 2: one thread per 2x2 block {p,q} x {p',q'} applies both rotations
+//            (S <- J^T S J), one thread per (row, pair) updates V <- V J.
+// Pairs follow the round-robin tournament on m' = m rounded up to even
+// (index m' - 1 is a dummy when m is odd).  Sweeps stop when every rotation
+// of a sweep was skipped (|s_pq| <= 1e-15 sqrt(|s_pp s_qq|)) or after 30.
+struct JacobiArgs {
+  double* S;  // m x m, ld = m, destroyed (diagonal = eigenvalues)
+  double* V;  // m x m, ld = m, eigenvectors
+  int m;
+  double* rc;  // m'/2
+  double* rs;  // m'/2
+  int* rot;    // [30]: rotations applied in each sweep (zeroed before launch)
+  GridBarrier bar;
+};
+
+__device__ __forceinline__ void rr_pair(int round, int i, int mp, int& p, int& q) {
+  // round-robin: player mp-1 fixed, others rotate
+  const int a = (i == 0) ? mp - 1 : (round + i) % (mp - 1);
+  const int b = (round + mp - 1 - i) % (mp - 1);
+  p = a < b ? a : b;
+  q = a < b ? b : a;
+}
+
+__global__ void jacobi_kernel(JacobiArgs a) {
+  grid_sync_init();
+  const int m = a.m, mp = m + (m & 1), np = mp / 2;
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x, nthr = int64_t(gridDim.x) * blockDim.x;
+  double* S = a.S;
+  double* V = a.V;
+  for (int64_t t = tid; t < int64_t(m) * m; t += nthr) V[t] = ((t % m) == (t / m)) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    if (!grid_sync(a.bar)) return;
+    for (int round = 0; round < mp - 1; ++round) {
+      for (int64_t i = tid; i < np; i += nthr) {
+        int p, q;
+        rr_pair(round, (int)i, mp, p, q);
+        double c = 1.0, s = 0.0;
+        if (q < m) {
+          const double apq = S[p + size_t(q) * m], app = S[p + size_t(p) * m], aqq = S[q + size_t(q) * m];
+          if (fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && apq != 0.0) {
+            const double th = (aqq - app) / (2.0 * apq);
+            const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+            atomicAdd(a.rot + sweep, 1);
+          }
+        }
+        a.rc[i] = c;
+        a.rs[i] = s;
+      }
+      if (!grid_sync(a.bar)) return;
+      // S <- J^T S J on 2x2 blocks, V <- V J
+      for (int64_t t = tid; t < int64_t(np) * np; t += nthr) {
+        const int i = int(t % np), j = int(t / np);
+        int p, q, p2, q2;
+        rr_pair(round, i, mp, p, q);
+        rr_pair(round, j, mp, p2, q2);
+        const double c1 = a.rc[i], s1 = a.rs[i], c2 = a.rc[j], s2 = a.rs[j];
+        const bool qv = q < m, q2v = q2 < m;
+        double x00 = S[p + size_t(p2) * m];
+        double x01 = q2v ? S[p + size_t(q2) * m] : 0.0;
+        double x10 = qv ? S[q + size_t(p2) * m] : 0.0;
+        double x11 = (qv && q2v) ? S[q + size_t(q2) * m] : 0.0;
+        // rows: [p; q] <- [c1 -s1; s1 c1]^T [p; q]
+        const double y00 = c1 * x00 - s1 * x10, y01 = c1 * x01 - s1 * x11;
+        const double y10 = s1 * x00 + c1 * x10, y11 = s1 * x01 + c1 * x11;
+        // columns: [p2 q2] <- [p2 q2] [c2 s2; -s2 c2]
+        S[p + size_t(p2) * m] = c2 * y00 - s2 * y01;
+        if (q2v) S[p + size_t(q2) * m] = s2 * y00 + c2 * y01;
+        if (qv) S[q + size_t(p2) * m] = c2 * y10 - s2 * y11;
+        if (qv && q2v) S[q + size_t(q2) * m] = s2 * y10 + c2 * y11;
+      }
+      for (int64_t t = tid; t < int64_t(m) * np; t += nthr) {
+        const int r = int(t % m), j = int(t / m);
+        int p, q;
+        rr_pair(round, j, mp, p, q);
+        if (q >= m) continue;
+        const double c = a.rc[j], s = a.rs[j];
+        const double vp = V[r + size_t(p) * m], vq = V[r + size_t(q) * m];
+        V[r + size_t(p) * m] = c * vp - s * vq;
+        V[r + size_t(q) * m] = s * vp + c * vq;
+      }
+      if (!grid_sync(a.bar)) return;
+    }
+    if (!grid_sync(a.bar)) return;
+    if (ld_acquire_int(a.rot + sweep) == 0) break;
+  }
+}
+
+__global__ void permute_cols_kernel(const double* A, int lda, int64_t nrows, const int* perm, int ncols, double* B,
+                                    int ldb) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < nrows * ncols;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = t % nrows;
+    const int c = int(t / nrows);
+    B[r + int64_t(c) * ldb] = A[r + int64_t(perm[c]) * lda];
+  }
+}
+
 // ------------------------------------------------------------ dense symmetric
 // Householder tridiagonalisation of A (n x n, lower part used), one block.
 // On exit: d, e; reflector k stored in column k of V (entries k+1..n-1) with tau[k].
@@ -711,6 +817,43 @@ int k_syev(double* A, int lda, int n, double* w, double* Z, int ldz, double* wor
   k_tri_eigvecs(d, e, n, w, Z, ldz, nullptr, st);
   ormtr_kernel<<<(n * 32 + 255) / 256, 256, 0, st>>>(A, lda, n, tau, Z, ldz, n);
   return 0;
+}
+
+int jacobi_max_grid() {
+  int dev = 0, nsm = 0, nb = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, jacobi_kernel, 256, 0);
+  return nb * nsm;
+}
+
+cudaError_t k_syev_jacobi(double* S, int m, double* V, double* work, int* iwork, GridBarrier bar, cudaStream_t st) {
+  JacobiArgs a;
+  a.S = S;
+  a.V = V;
+  a.m = m;
+  a.rc = work;
+  a.rs = work + (m / 2 + 1);
+  a.rot = iwork;
+  a.bar = bar;
+  cudaMemsetAsync(iwork, 0, 30 * sizeof(int), st);
+  cudaMemsetAsync(bar.count, 0, sizeof(unsigned), st);
+  static int grid = 0;
+  if (grid == 0) grid = jacobi_max_grid();
+  int g = grid;
+  const int64_t need = (int64_t(m + 1) * (m + 1) / 4 + 255) / 256;
+  if (g > need) g = (int)need;
+  if (g < 1) g = 1;
+  void* args[] = {(void*)&a};
+  return cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(g), dim3(256), args, 0, st);
+}
+
+void k_permute_cols(const double* A, int lda, int64_t nrows, const int* perm, int ncols, double* B, int ldb,
+                    cudaStream_t st) {
+  int64_t b = (nrows * ncols + 255) / 256;
+  if (b > 8192) b = 8192;
+  if (b < 1) b = 1;
+  permute_cols_kernel<<<(int)b, 256, 0, st>>>(A, lda, nrows, perm, ncols, B, ldb);
 }
 
 void k_potrf_upper(double* A, int lda, int n, int* dev_status, cudaStream_t st) {

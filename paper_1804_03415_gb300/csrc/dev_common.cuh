@@ -10,8 +10,8 @@ namespace mmd {
 enum DevStatus : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BREAKDOWN = 2, DEV_NOTSPD = 3 };
 
 struct GridBarrier {
-  unsigned int* count;  // arrivals in the current phase
-  unsigned int* gen;    // phase counter
+  unsigned int* count;  // monotone arrival counter (zeroed before each launch)
+  unsigned int* gen;    // unused (kept for layout)
   int* status;          // set to DEV_TIMEOUT when a wait gives up
   long long timeout_ns; // limit of one wait
 };
@@ -34,39 +34,47 @@ __device__ __forceinline__ int ld_acquire_int(const int* p) {
   return v;
 }
 
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
-// last block to arrive resets the count and advances the phase; the others
-// wait for the phase to change, for at most timeout_ns.  On timeout the
-// status word is set; the function then returns false on every block that
-// sees the status (callers leave the kernel).  Returns true when all blocks
-// passed.
-__device__ __forceinline__ bool grid_sync(const GridBarrier& b) {
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Phase counter of the grid barrier, one per block.
+__shared__ unsigned g_bar_phase;
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).
+// The counter only grows: phase t of the launch is complete when it reaches
+// t * gridDim.  One release-add per block, then an acquire poll with a short
+// sleep between polls (the counter lives on its own 128-byte line).  A wait
+// gives up after timeout_ns: the status word is set and every block that
+// sees it returns false (callers leave the kernel), so the launch ends in
+// bounded time.  The counter is zeroed before every launch and
+// grid_sync_init() must run at kernel entry.
+__device__ __forceinline__ void grid_sync_init() {
+  if (threadIdx.x == 0) g_bar_phase = 0;
   __syncthreads();
+}
+
+__device__ __forceinline__ bool grid_sync(const GridBarrier& b) {
   __shared__ int s_ok;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned g = ld_acquire(b.gen);
-    __threadfence();
     const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
-    const unsigned arrived = atomicAdd(b.count, 1u);
+    const unsigned target = (++g_bar_phase) * nb;
+    __threadfence();
+    red_release_add(b.count, 1u);
     int ok = 1;
-    if (arrived == nb - 1) {
-      atomicExch(b.count, 0u);
-      __threadfence();
-      atomicAdd(b.gen, 1u);
-    } else {
-      const long long t0 = global_ns();
-      unsigned spins = 0;
-      while (ld_acquire(b.gen) == g) {
-        if (((++spins) & 63u) == 0u) {
-          if (ld_acquire_int(b.status) != DEV_OK || global_ns() - t0 > b.timeout_ns) {
-            atomicExch(b.status, (int)DEV_TIMEOUT);
-            ok = 0;
-            break;
-          }
+    const long long t0 = global_ns();
+    unsigned spins = 0;
+    while (ld_acquire(b.count) < target) {
+      __nanosleep(20);
+      if (((++spins) & 255u) == 0u) {
+        if (ld_acquire_int(b.status) != DEV_OK || global_ns() - t0 > b.timeout_ns) {
+          atomicExch(b.status, (int)DEV_TIMEOUT);
+          ok = 0;
+          break;
         }
       }
     }
-    __threadfence();
     if (ok && ld_acquire_int(b.status) != DEV_OK) ok = 0;
     s_ok = ok;
   }

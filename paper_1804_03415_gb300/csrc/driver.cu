@@ -12,7 +12,9 @@
 //     level 0 tests are relative to the residual target;
 //   * Lanczos breakdown ||f||_M < 1e-10 ||w||_M draws a SplitMix64 vector;
 //   * CGS2 re-orthogonalisation against [V_ini, V] in the M inner product;
-//   * exact shifts after the p-step extension, p = c_r d;
+//   * exact shifts after the p-step extension, p = max(c_r d, k) (k = current
+//     dimension: the factorisation doubles before the shifts);
+//   * refinement window: mu_mh >= max(mu_re, mu_ml alpha / (1 + beta));
 //   * column-scaled CholQR2 for the M-QR, S symmetrised, stop test
 //     ||Q_mh - Q'_mh (Q'_mh^T M Q_mh)||_F < eps / sqrt(1 + eps_h delta_h).
 // Differences from the paper's own CPU design (same mathematics):
@@ -101,8 +103,8 @@ Workspace* get_ws(mmd_handle* h) {
   cudaDeviceProp pr;
   CK(cudaGetDeviceProperties(&pr, h->device));
   ws->nsm = pr.multiProcessorCount;
-  CK(cudaMalloc(&ws->bar, 4 * sizeof(unsigned)));
-  CK(cudaMemset(ws->bar, 0, 4 * sizeof(unsigned)));
+  CK(cudaMalloc(&ws->bar, 64 * sizeof(unsigned)));
+  CK(cudaMemset(ws->bar, 0, 64 * sizeof(unsigned)));
   CK(cudaMalloc(&ws->status, sizeof(int)));
   CK(cudaMemset(ws->status, 0, sizeof(int)));
   CK(cudaMalloc(&ws->red, sizeof(double) * 4 * 8 * 512));
@@ -113,7 +115,18 @@ Workspace* get_ws(mmd_handle* h) {
   return ws;
 }
 
-int tpr_of(const DCSR& A) { return A.mean_row <= 6.0 ? 4 : (A.mean_row <= 16.0 ? 8 : 32); }
+Sell sell_of(const DCSR& A) {
+  Sell s;
+  s.nrows = A.nrows;
+  s.nslices = A.nslices;
+  s.ptr = A.s_ptr;
+  s.len = A.s_len;
+  s.row = A.s_row;
+  s.col = A.s_col;
+  s.val = A.s_val;
+  s.val32 = A.s_val32;
+  return s;
+}
 
 // ------------------------------------------------------------ context
 struct Ctx {
@@ -157,7 +170,7 @@ struct Ctx {
       return;
     }
     const DCSR& A = which ? L.M : L.A;
-    k_spmv(A.rowptr, A.col, A.val, L.n, x, L.n, y, L.n, m, tpr_of(A), st);
+    k_spmv(sell_of(A), x, L.n, y, L.n, m, st);
     after_launch();
   }
   void dots(const double* x, const double* y, int64_t n, int m, double* out_dev) {
@@ -176,25 +189,93 @@ struct Ctx {
 
   // ---- the persistent solver
   // mode 0: CG on A_k; 1: flexible PCG with M_k; 2: CG on P A_k P (patches of level k+1)
-  // B: rhs (n x m, ld n); X: initial guess (x0 = 1) / solution
+  // B: rhs (n x m, ld n); X: initial guess (x0 = 1) / solution.  In the mixed
+  // mode the FP32 solver runs inside FP64 iterative refinement.
   void solve(int k, int mode, const double* B, double* X, int m, int x0, double tol, int maxit,
              std::vector<int64_t>* iters, int64_t* inner_total, int* notconv) {
+    if (o.precision == MMD_MIXED) {
+      solve_mixed(k, mode, B, X, m, x0, tol, maxit, iters, inner_total, notconv);
+      return;
+    }
+    solve_raw(k, mode, false, B, X, m, x0, tol, maxit, iters, inner_total, notconv);
+  }
+
+  // FP64 iterative refinement: R = B - A X in FP64, FP32 solve A D = R to a
+  // relative tolerance no tighter than 1e-5, X += D; until ||R|| <= tol ||B||.
+  void solve_mixed(int k, int mode, const double* B, double* X, int m, int x0, double tol, int maxit,
+                   std::vector<int64_t>* iters, int64_t* inner_total, int* notconv) {
+    const DLevel& L = h->dl[k];
+    const int64_t n = L.n;
+    double* R = buf<double>(ws, "mx_R", size_t(n) * m);
+    double* Y = buf<double>(ws, "mx_Y", size_t(n) * m);
+    float* B32 = buf<float>(ws, "mx_B32", size_t(n) * m);
+    float* D32 = buf<float>(ws, "mx_D32", size_t(n) * m);
+    if (!x0) {
+      k_fill(X, n * m, 0.0, st);
+      after_launch();
+    }
+    std::vector<double> bn = dots_host(B, B, n, m);
+    for (auto& v : bn) v = std::sqrt(std::max(v, 0.0));
+    std::vector<int64_t> itsum(m, 0);
+    bool done = false;
+    for (int ref = 0; ref < 12; ++ref) {
+      spmv(k, 0, X, Y, m);
+      k_sub(R, B, Y, n * m, st);
+      after_launch();
+      if (mode == 2) {
+        k_project(R, n, m, L.seg_ptr, L.phi_next, L.nseg, st);
+        after_launch();
+      }
+      std::vector<double> rn = dots_host(R, R, n, m);
+      double need = 1.0;
+      bool all = true;
+      for (int c = 0; c < m; ++c) {
+        rn[c] = std::sqrt(std::max(rn[c], 0.0));
+        if (rn[c] <= tol * bn[c] || bn[c] == 0.0) {
+          k_fill(R + size_t(c) * n, n, 0.0, st);  // converged column: zero rhs, no work
+          after_launch();
+        } else {
+          all = false;
+          need = std::min(need, tol * bn[c] / rn[c]);
+        }
+      }
+      if (all) {
+        done = true;
+        break;
+      }
+      const double tin = std::min(0.5, std::max(1e-5, 0.5 * need));
+      k_to_f32(B32, R, n * m, st);
+      after_launch();
+      std::vector<int64_t> its;
+      solve_raw(k, mode, true, B32, D32, m, 0, tin, maxit, &its, inner_total, nullptr);
+      for (int c = 0; c < m; ++c) itsum[c] += its[c];
+      k_add_f32(X, D32, n * m, st);
+      after_launch();
+    }
+    if (iters)
+      for (int c = 0; c < m; ++c) iters->push_back(itsum[c]);
+    if (!done && notconv) ++*notconv;
+  }
+
+  void solve_raw(int k, int mode, bool fp32, const void* B, void* X, int m, int x0, double tol, int maxit,
+                 std::vector<int64_t>* iters, int64_t* inner_total, int* notconv) {
     const DLevel& L = h->dl[k];
     const int64_t n = L.n;
     const int MT = (m > 1) ? 8 : 1;
-    const int tpr = tpr_of(L.A);
-    const int grid = solver_max_grid(tpr, MT, ws->nsm);
+    const int grid = solver_max_grid(MT, ws->nsm);
     if (grid < 1) {
       set_error("solver kernel cannot be made resident");
       throw CudaFail{MMD_ECUDA};
     }
-    double* r = buf<double>(ws, "sv_r", size_t(n) * MT);
-    double* p = buf<double>(ws, "sv_p", size_t(n) * MT);
-    double* q = buf<double>(ws, "sv_q", size_t(n) * MT);
-    double* z = buf<double>(ws, "sv_z", size_t(n) * MT);
-    double* ir = buf<double>(ws, "sv_ir", size_t(n) * MT);
-    double* ip = buf<double>(ws, "sv_ip", size_t(n) * MT);
-    double* iq = buf<double>(ws, "sv_iq", size_t(n) * MT);
+    const size_t eb = fp32 ? sizeof(float) : sizeof(double);
+    const std::string pre = fp32 ? "sv32_" : "sv_";
+    void* r = buf<char>(ws, pre + "r", size_t(n) * MT * eb);
+    void* p = buf<char>(ws, pre + "p", size_t(n) * MT * eb);
+    void* q = buf<char>(ws, pre + "q", size_t(n) * MT * eb);
+    void* z = buf<char>(ws, pre + "z", size_t(n) * MT * eb);
+    void* ir = buf<char>(ws, pre + "ir", size_t(n) * MT * eb);
+    void* ip = buf<char>(ws, pre + "ip", size_t(n) * MT * eb);
+    void* iq = buf<char>(ws, pre + "iq", size_t(n) * MT * eb);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     for (int c0 = 0; c0 < m; c0 += MT) {
       const int mc = std::min(MT, m - c0);
@@ -202,14 +283,8 @@ struct Ctx {
       std::memset(&a, 0, sizeof(a));
       a.mode = mode;
       a.n = n;
-      a.arp = L.A.rowptr;
-      a.acol = L.A.col;
-      a.aval = L.A.val;
-      if (mode == 1) {
-        a.mrp = L.M.rowptr;
-        a.mcol = L.M.col;
-        a.mval = L.M.val;
-      }
+      a.A = sell_of(L.A);
+      if (mode == 1) a.M = sell_of(L.M);
       if (mode == 2) {
         a.seg_ptr = L.seg_ptr;
         a.phi = L.phi_next;
@@ -217,8 +292,8 @@ struct Ctx {
       }
       a.m = mc;
       a.ld = n;
-      a.b = B + size_t(c0) * n;
-      a.x = X + size_t(c0) * n;
+      a.b = (const char*)B + size_t(c0) * n * eb;
+      a.x = (char*)X + size_t(c0) * n * eb;
       a.x0 = x0;
       a.r = r;
       a.p = p;
@@ -227,6 +302,7 @@ struct Ctx {
       a.ir = ir;
       a.ip = ip;
       a.iq = iq;
+      a.fp32 = fp32 ? 1 : 0;
       a.tol = tol;
       a.itol = 0.1 * tol;
       a.maxit = maxit;
@@ -236,16 +312,17 @@ struct Ctx {
       a.in_out = ws->in_out;
       a.conv = ws->conv;
       a.bar.count = ws->bar;
-      a.bar.gen = ws->bar + 1;
+      a.bar.gen = ws->bar + 32;
       a.bar.status = ws->status;
       a.bar.timeout_ns = (long long)timeout_ns;
       CK(cudaMemsetAsync(ws->in_out, 0, sizeof(int64_t), st));
+      CK(cudaMemsetAsync(ws->bar, 0, sizeof(unsigned), st));
       if (o.profile) {
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         CK(cudaEventRecord(e0, st));
       }
-      CK(launch_solver(a, tpr, MT, grid, st));
+      CK(launch_solver(a, MT, grid, st));
       after_launch();
       if (o.profile) CK(cudaEventRecord(e1, st));
       int64_t its[8], inn = 0;
@@ -271,11 +348,11 @@ struct Ctx {
         S.pcg_ms += ms;
         // algorithmic bytes: matrix once per iteration, vectors per active column
         const double zA = (double)L.A.nnz, nn = (double)n;
-        double bytes = itmax * (12.0 * zA + 4.0 * nn) + itsum * 72.0 * nn;
+        const double mb = fp32 ? 8.0 : 12.0, vb = fp32 ? 4.0 : 8.0;
+        double bytes = itmax * (mb * zA + 4.0 * nn) + itsum * 9.0 * vb * nn;
         if (mode == 1) {
           const double zM = (double)L.M.nnz;
-          // inner iterations: counted in total over columns; matrix traffic bounded by one per column-iteration
-          bytes += (double)inn * (12.0 * zM / std::max(mc, 1) + 60.0 * nn);
+          bytes += (double)inn * (mb * zM / std::max(mc, 1) + 7.5 * vb * nn);
         }
         S.pcg_bytes += bytes;
       }
@@ -298,6 +375,34 @@ struct Ctx {
     return its[0];
   }
 };
+
+// Symmetric eigen-decomposition of S (m x m, destroyed) by parallel Jacobi;
+// eigenvalues sorted descending (host) and eigenvectors in that order (P).
+void sym_eig_desc(Ctx& c, double* S, int m, std::vector<double>& w, double* P) {
+  double* V = buf<double>(c.ws, "je_V", size_t(m) * m);
+  double* wk = buf<double>(c.ws, "je_w", m + 8);
+  int* iw = buf<int>(c.ws, "je_i", 64);
+  int* pd = buf<int>(c.ws, "je_p", m);
+  GridBarrier bar;
+  bar.count = c.ws->bar;
+  bar.gen = c.ws->bar + 32;
+  bar.status = c.ws->status;
+  bar.timeout_ns = (long long)c.timeout_ns;
+  CK(k_syev_jacobi(S, m, V, wk, iw, bar, c.st));
+  c.after_launch();
+  std::vector<double> d(m);
+  CK(cudaMemcpy2DAsync(d.data(), sizeof(double), S, sizeof(double) * (m + 1), sizeof(double), m,
+                       cudaMemcpyDeviceToHost, c.st));
+  c.check_status();
+  std::vector<int> ord(m);
+  for (int i = 0; i < m; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return d[a] > d[b]; });
+  w.resize(m);
+  for (int i = 0; i < m; ++i) w[i] = d[ord[i]];
+  CK(cudaMemcpyAsync(pd, ord.data(), sizeof(int) * m, cudaMemcpyHostToDevice, c.st));
+  k_permute_cols(V, m, m, pd, m, P, m, c.st);
+  c.after_launch();
+}
 
 // ------------------------------------------------------------ M-Lanczos (Algorithm 3)
 struct Lanczos {
@@ -485,7 +590,7 @@ ExtendOut extend(Ctx& c, int k, double* BAS, int m0, int cap, const std::vector<
       std::vector<double> th, res;
       lz.ritz(th, res);
       if (res_ok(th, res)) return;
-      const int pe = std::min(pp, room - lz.j);
+      const int pe = std::min(std::max(pp, lz.j), room - lz.j);
       if (pe <= 0) return;
       const int kk = lz.j;
       for (int s = 0; s < pe; ++s) lz.step(pcg_tol, breakdown);
@@ -572,10 +677,7 @@ int refine(Ctx& c, int k, double* Q0, std::vector<double>& D, double tol_rel, do
   double* Dd = buf<double>(c.ws, "rf_D", m);
   double* Sm = buf<double>(c.ws, "rf_S", size_t(m) * m);
   double* P = buf<double>(c.ws, "rf_P", size_t(m) * m);
-  double* Y = buf<double>(c.ws, "rf_Y", size_t(m) * m);
   double* X = buf<double>(c.ws, "rf_X", size_t(m) * m);
-  double* wv = buf<double>(c.ws, "rf_w", m);
-  double* sywork = buf<double>(c.ws, "rf_sywork", size_t(6) * m + 16);
   const size_t gsl = std::max<size_t>(size_t(8) << 20, size_t(m) * m * 4);
   double* gs = buf<double>(c.ws, "gemm_scratch", gsl);
   // g_i = CG(B, U^T M q_i): in coordinates U g, rhs = P M q_i
@@ -618,20 +720,18 @@ int refine(Ctx& c, int k, double* Q0, std::vector<double>& D, double tol_rel, do
       c.S.inner_iters += inner;
       c.S.not_converged += nc;
     }
-    // S = W^T F, eig descending
+    // S = W^T F, eig descending (parallel Jacobi)
     k_gemm_tn(m, m, n, 1.0, W, n, F, n, 0.0, Sm, m, gs, gsl, c.st);
     k_symmetrise(Sm, m, m, c.st);
-    k_syev(Sm, m, m, wv, Y, m, sywork, c.ws->status, c.st);
-    c.S.kernel_launches += 9;
-    std::vector<double> w(m);
-    CK(cudaMemcpyAsync(w.data(), wv, sizeof(double) * m, cudaMemcpyDeviceToHost, c.st));
-    for (int i = 0; i < m; ++i)
-      CK(cudaMemcpyAsync(P + size_t(i) * m, Y + size_t(m - 1 - i) * m, sizeof(double) * m,
-                         cudaMemcpyDeviceToDevice, c.st));
-    c.check_status();
-    for (int i = 0; i < m; ++i) D[i] = w[m - 1 - i];
+    c.S.kernel_launches += 3;
+    std::vector<double> w;
+    sym_eig_desc(c, Sm, m, w, P);
+    for (int i = 0; i < m; ++i) D[i] = w[i];
+    // renew m_h: mu_mh >= mu_re, and a gap to the end of the window
+    // (mu_mh >= mu_ml alpha / (1 + beta), efficiency condition (ii) of Section 6)
+    const double thr = std::max(mu_re, D[m - 1] * c.o.alpha / (1.0 + c.o.beta));
     mh = 0;
-    while (mh < m && D[mh] >= mu_re) ++mh;
+    while (mh < m && D[mh] >= thr) ++mh;
     // Q <- Q P, F <- F P, MQ = W P
     k_gemm_nn(n, m, m, 1.0, Q, n, P, m, 0.0, T1, n, c.st);
     std::swap(Q, T1);
@@ -672,8 +772,6 @@ void coarsest(Ctx& c, int K, std::vector<double>& mu, double* Zout) {
   double* Md = buf<double>(c.ws, "co_M", size_t(n) * n);
   double* Tt = buf<double>(c.ws, "co_T", size_t(n) * n);
   double* Y = buf<double>(c.ws, "co_Y", size_t(n) * n);
-  double* w = buf<double>(c.ws, "co_w", n);
-  double* sywork = buf<double>(c.ws, "rf_sywork", size_t(6) * n + 16);
   k_csr_to_dense(L.A.rowptr, L.A.col, L.A.val, n, Ad, n, c.st);
   c.after_launch();
   if (K > 0) {
@@ -687,18 +785,24 @@ void coarsest(Ctx& c, int K, std::vector<double>& mu, double* Zout) {
   } else {
     CK(cudaMemcpyAsync(Tt, Ad, sizeof(double) * size_t(n) * n, cudaMemcpyDeviceToDevice, c.st));
   }
-  k_syev(Tt, n, n, w, Y, n, sywork, c.ws->status, c.st);
-  c.S.kernel_launches += 7;
+  // eigenvalues of C = L^{-1} A L^{-T}; Jacobi sorted descending in lambda, so
+  // reverse to ascending lambda = descending mu
+  std::vector<double> wd;
+  sym_eig_desc(c, Tt, n, wd, Tt == Y ? nullptr : Y);
+  std::vector<int> rev(n);
+  for (int i = 0; i < n; ++i) rev[i] = n - 1 - i;
+  int* pd = buf<int>(c.ws, "co_rev", n);
+  CK(cudaMemcpyAsync(pd, rev.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c.st));
+  k_permute_cols(Y, n, n, pd, n, Ad, n, c.st);  // Ad <- Y reversed (A no longer needed)
+  c.after_launch();
   if (K > 0) {
-    k_trsm_lltn(Md, n, n, Y, n, n, c.st);  // z = L^{-T} y
+    k_trsm_lltn(Md, n, n, Ad, n, n, c.st);  // z = L^{-T} y
     c.after_launch();
   }
-  std::vector<double> lam(n);
-  CK(cudaMemcpyAsync(lam.data(), w, sizeof(double) * n, cudaMemcpyDeviceToHost, c.st));
   c.check_status();
-  // descending mu = ascending lambda order (the order of the columns of Y)
   mu.resize(n);
-  for (int i = 0; i < n; ++i) mu[i] = 1.0 / lam[i];
+  for (int i = 0; i < n; ++i) mu[i] = 1.0 / wd[n - 1 - i];
+  Y = Ad;
   CK(cudaMemcpyAsync(Zout, Y, sizeof(double) * size_t(n) * n, cudaMemcpyDeviceToDevice, c.st));
 }
 
@@ -842,8 +946,7 @@ int run_eig(mmd_handle* h, int N, double tol, const mmd_eig_opts& o, double* lam
         // transfer V <- Psi^(k+1) V (Algorithm 6, coefficient reform)
         double* Q0 = buf<double>(c.ws, "Q0", size_t(n) * std::max(m, 1));
         if (m) {
-          const DCSR& P = h->dl[k + 1].psi;
-          k_spmv(P.rowptr, P.col, P.val, n, Vh, h->dl[k + 1].n, Q0, n, m, 8, st);
+          k_spmv(sell_of(h->dl[k + 1].psi), Vh, h->dl[k + 1].n, Q0, n, m, st);
           c.after_launch();
         }
         double eps_h = 0, delta_h = 0, tol_rel, eps_abs = 0;
@@ -894,8 +997,7 @@ int run_eig(mmd_handle* h, int N, double tol, const mmd_eig_opts& o, double* lam
       k_normalise_sign(Vn, n0, n0, nout, nullptr, st);
       k_gather(Vn, n0, h->dl[0].d_perm, n0, nout, Vs, n0, st);
       CK(cudaMemcpyAsync(lamd, lam.data(), sizeof(double) * nout, cudaMemcpyHostToDevice, st));
-      const DCSR& A = h->dl[0].A;
-      k_residuals(A.rowptr, A.col, A.val, n0, Vs, n0, nout, lamd, resd, rsc, st);
+      k_residuals(sell_of(h->dl[0].A), n0, Vs, n0, nout, lamd, resd, rsc, st);
       c.S.kernel_launches += 3 + 4;
     }
     std::vector<double> res(nout);

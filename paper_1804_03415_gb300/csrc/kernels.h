@@ -8,25 +8,34 @@
 
 namespace mmd {
 
+// SELL-32 view of a sparse matrix (see DCSR).
+struct Sell {
+  int64_t nrows = 0;
+  int64_t nslices = 0;
+  const int32_t* ptr = nullptr;
+  const int32_t* len = nullptr;
+  const int32_t* row = nullptr;
+  const int32_t* col = nullptr;
+  const double* val = nullptr;
+  const float* val32 = nullptr;
+};
+
 struct SolverArgs {
   int mode;  // 0 CG, 1 flexible PCG with inner CG on M, 2 CG on P A P
   int64_t n;
-  const int32_t* arp;
-  const int32_t* acol;
-  const double* aval;
-  const int32_t* mrp;
-  const int32_t* mcol;
-  const double* mval;
+  Sell A;
+  Sell M;
   const int32_t* seg_ptr;
   const double* phi;
   int64_t nseg;
   int m;
   int64_t ld;
-  const double* b;
-  double* x;
+  const void* b;   // T = double, or float when fp32 = 1
+  void* x;
   int x0;
-  double *r, *p, *q, *z;
-  double *ir, *ip, *iq;
+  void *r, *p, *q, *z;
+  void *ir, *ip, *iq;
+  int fp32;        // 1: FP32 instance (matrix val32, FP32 vectors)
   double tol, itol;
   int maxit, imaxit;
   double* red;         // [4][MT][grid]
@@ -37,8 +46,8 @@ struct SolverArgs {
 };
 
 int solver_threads();
-int solver_max_grid(int tpr, int mt, int num_sms);
-cudaError_t launch_solver(const SolverArgs& a, int tpr, int mt, int grid, cudaStream_t st);
+int solver_max_grid(int mt, int num_sms);
+cudaError_t launch_solver(const SolverArgs& a, int mt, int grid, cudaStream_t st);
 
 // ---- vector / sparse kernels (blas.cu)
 void k_fill(double* x, int64_t n, double v, cudaStream_t st);
@@ -46,9 +55,8 @@ void k_copy(double* y, const double* x, int64_t n, cudaStream_t st);
 void k_scal(double* x, int64_t n, double a, cudaStream_t st);
 void k_scal_dev(double* x, int64_t n, const double* a, int invert, cudaStream_t st);
 void k_axpy(double* y, const double* x, int64_t n, double a, cudaStream_t st);
-// y = A x (CSR), columns m of ld (x, y column-major)
-void k_spmv(const int32_t* rp, const int32_t* ci, const double* va, int64_t nrows, const double* x, int64_t ldx,
-            double* y, int64_t ldy, int m, int tpr, cudaStream_t st);
+// y = A x (SELL-32), columns m of ld (x, y column-major)
+void k_spmv(const Sell& A, const double* x, int64_t ldx, double* y, int64_t ldy, int m, cudaStream_t st);
 // dot products: out[c] = sum_i x(i,c) y(i,c), deterministic two-stage; scratch >= 1024*m doubles
 void k_dots(const double* x, const double* y, int64_t n, int64_t ld, int m, double* out, double* scratch,
             cudaStream_t st);
@@ -72,6 +80,10 @@ void k_scatter(const double* x, int64_t ldx, const int32_t* perm, int64_t n, int
 // project each column onto range(P): x -= phi (phi^T x) per segment
 void k_project(double* x, int64_t ld, int m, const int32_t* seg_ptr, const double* phi, int64_t nseg,
                cudaStream_t st);
+// r = b - y (FP64); f = (float) d; x += (double) f  (n x m, ld n)
+void k_sub(double* r, const double* b, const double* y, int64_t n, cudaStream_t st);
+void k_to_f32(float* f, const double* d, int64_t n, cudaStream_t st);
+void k_add_f32(double* x, const float* f, int64_t n, cudaStream_t st);
 // columns: x(:,c) *= s[c]
 void k_scale_cols(double* x, int64_t ld, int64_t n, int m, const double* s, cudaStream_t st);
 // SplitMix64 counter random vector in [-1, 1)
@@ -80,8 +92,8 @@ void k_random(double* x, int64_t n, uint64_t seed, uint64_t stream, const int32_
 // sign fix + normalise columns (largest |.| positive, ties lowest index)
 void k_normalise_sign(double* V, int64_t ld, int64_t n, int m, double* scratch, cudaStream_t st);
 // residual norms ||A v - l v||: out[c]
-void k_residuals(const int32_t* rp, const int32_t* ci, const double* va, int64_t n, const double* V, int64_t ld,
-                 int m, const double* lam, double* out, double* scratch, cudaStream_t st);
+void k_residuals(const Sell& A, int64_t n, const double* V, int64_t ld, int m, const double* lam, double* out,
+                 double* scratch, cudaStream_t st);
 
 // ---- small dense (dense.cu); all matrices column-major
 // eigenvalues of symmetric tridiagonal (d: n, e: n-1) by bisection, ascending
@@ -99,6 +111,12 @@ void k_tri_qr_sweeps(double* d, double* e, int n, const double* sh, int p, doubl
 // dense symmetric eig: A (n x n) -> w ascending, Z eigenvectors (may alias A). work: >= 4 n^2 + 8 n doubles
 int k_syev(double* A, int lda, int n, double* w, double* Z, int ldz, double* work, int* dev_status,
            cudaStream_t st);
+// parallel two-sided Jacobi (cooperative): S (m x m, ld m) -> diagonal (eigenvalues, unsorted),
+// V (m x m) eigenvectors; work >= m + 4 doubles, iwork >= 30 ints
+cudaError_t k_syev_jacobi(double* S, int m, double* V, double* work, int* iwork, GridBarrier bar, cudaStream_t st);
+// B(:, c) = A(:, perm[c])
+void k_permute_cols(const double* A, int lda, int64_t nrows, const int* perm, int ncols, double* B, int ldb,
+                    cudaStream_t st);
 // Cholesky A = R^T R (upper R in place), status set on failure; Rinv = R^{-1} upper
 void k_potrf_upper(double* A, int lda, int n, int* dev_status, cudaStream_t st);
 void k_trinv_upper(const double* R, int ldr, int n, double* Rinv, int ldri, cudaStream_t st);

@@ -28,7 +28,8 @@ struct HLevel {
   int used_closed = 0;
 };
 
-// Device CSR (device order).
+// Device CSR (device order) plus its SELL-32 copy (slices of 32 rows, rows
+// sorted by length inside windows of 256, entries column-major in a slice).
 struct DCSR {
   int64_t nrows = 0, ncols = 0, nnz = 0;
   int32_t* rowptr = nullptr;
@@ -37,6 +38,13 @@ struct DCSR {
   float* val32 = nullptr;
   double mean_row = 0;
   int max_row = 0;
+  int64_t nslices = 0, sell_nnz = 0;
+  int32_t* s_ptr = nullptr;   // nslices + 1, offsets of the slices
+  int32_t* s_len = nullptr;   // nslices, width of each slice
+  int32_t* s_row = nullptr;   // 32 * nslices, row of each lane (-1 = padding)
+  int32_t* s_col = nullptr;   // sell_nnz
+  double* s_val = nullptr;    // sell_nnz
+  float* s_val32 = nullptr;   // sell_nnz
 };
 
 // Device level data.  Level k's vectors are stored in "device order": the
