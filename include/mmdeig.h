@@ -101,7 +101,8 @@ typedef struct {
   int64_t b_calls, b_iters;                      /* CG on B^(k) (Alg 5) */
   int64_t refine_pcg_calls, refine_pcg_iters;    /* warm-started PCG in Alg 5 */
   int64_t restarts, lanczos_steps, refine_iters; /* Alg 2, Alg 3, Alg 5 */
-  int64_t not_converged;                         /* capped loops */
+  int64_t not_converged;                         /* capped loops (sum of the three below) */
+  int64_t nc_solve, nc_restart, nc_refine;       /* capped CG/PCG solves, restart loops, refinements */
   int64_t kernel_launches;                       /* CUDA kernels launched */
   int n_levels;                                  /* K + 1 */
   int n_converged;                               /* pairs meeting the residual target */

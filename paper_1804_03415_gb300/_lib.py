@@ -41,7 +41,8 @@ class mmd_eig_stats(C.Structure):
     _fields_ = [("op_calls", C.c_int64), ("pcg_iters", C.c_int64), ("inner_iters", C.c_int64),
                 ("b_calls", C.c_int64), ("b_iters", C.c_int64), ("refine_pcg_calls", C.c_int64),
                 ("refine_pcg_iters", C.c_int64), ("restarts", C.c_int64), ("lanczos_steps", C.c_int64),
-                ("refine_iters", C.c_int64), ("not_converged", C.c_int64), ("kernel_launches", C.c_int64),
+                ("refine_iters", C.c_int64), ("not_converged", C.c_int64), ("nc_solve", C.c_int64),
+                ("nc_restart", C.c_int64), ("nc_refine", C.c_int64), ("kernel_launches", C.c_int64),
                 ("n_levels", C.c_int), ("n_converged", C.c_int), ("norm_A", C.c_double),
                 ("max_rel_residual", C.c_double), ("mu1", C.c_double), ("t_total_ms", C.c_double),
                 ("pcg_launches", C.c_int64), ("pcg_ms", C.c_double), ("pcg_bytes", C.c_double)]

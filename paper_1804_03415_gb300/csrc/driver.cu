@@ -204,6 +204,10 @@ struct Ctx {
   // relative tolerance no tighter than 1e-5, X += D; until ||R|| <= tol ||B||.
   void solve_mixed(int k, int mode, const double* B, double* X, int m, int x0, double tol, int maxit,
                    std::vector<int64_t>* iters, int64_t* inner_total, int* notconv) {
+    if (mode == 0) {  // level-0 CG: FP32 recurrences with FP64 reliable updates, one launch
+      solve_raw(k, 0, true, nullptr, nullptr, m, x0, tol, maxit, iters, inner_total, notconv, B, X);
+      return;
+    }
     const DLevel& L = h->dl[k];
     const int64_t n = L.n;
     double* R = buf<double>(ws, "mx_R", size_t(n) * m);
@@ -258,7 +262,8 @@ struct Ctx {
   }
 
   void solve_raw(int k, int mode, bool fp32, const void* B, void* X, int m, int x0, double tol, int maxit,
-                 std::vector<int64_t>* iters, int64_t* inner_total, int* notconv) {
+                 std::vector<int64_t>* iters, int64_t* inner_total, int* notconv, const double* B64 = nullptr,
+                 double* X64 = nullptr) {
     const DLevel& L = h->dl[k];
     const int64_t n = L.n;
     const int MT = (m > 1) ? 8 : 1;
@@ -292,8 +297,10 @@ struct Ctx {
       }
       a.m = mc;
       a.ld = n;
-      a.b = (const char*)B + size_t(c0) * n * eb;
-      a.x = (char*)X + size_t(c0) * n * eb;
+      a.b = B ? (const char*)B + size_t(c0) * n * eb : nullptr;
+      a.x = X ? (char*)X + size_t(c0) * n * eb : nullptr;
+      a.b64 = B64 ? B64 + size_t(c0) * n : nullptr;
+      a.x64 = X64 ? X64 + size_t(c0) * n : nullptr;
       a.x0 = x0;
       a.r = r;
       a.p = p;
@@ -372,6 +379,7 @@ struct Ctx {
     S.pcg_iters += its[0];
     S.inner_iters += inner;
     S.not_converged += nc;
+    S.nc_solve += nc;
     return its[0];
   }
 };
@@ -597,6 +605,7 @@ ExtendOut extend(Ctx& c, int k, double* BAS, int m0, int cap, const std::vector<
       lz.restart(kk, pe);
     }
     c.S.not_converged += 1;
+    c.S.nc_restart += 1;
   };
   const int p = std::max(1, c.o.c_r * d);
   while (true) {
@@ -691,6 +700,7 @@ int refine(Ctx& c, int k, double* Q0, std::vector<double>& D, double tol_rel, do
     c.S.b_calls += m;
     for (auto t : its) c.S.b_iters += t;
     c.S.not_converged += nc;
+    c.S.nc_solve += nc;
   }
   // F0 = Q0 D + U G
   CK(cudaMemcpyAsync(Dd, D.data(), sizeof(double) * m, cudaMemcpyHostToDevice, c.st));
@@ -719,6 +729,7 @@ int refine(Ctx& c, int k, double* Q0, std::vector<double>& D, double tol_rel, do
       for (auto t : its) c.S.refine_pcg_iters += t;
       c.S.inner_iters += inner;
       c.S.not_converged += nc;
+      c.S.nc_solve += nc;
     }
     // S = W^T F, eig descending (parallel Jacobi)
     k_gemm_tn(m, m, n, 1.0, W, n, F, n, 0.0, Sm, m, gs, gsl, c.st);
@@ -756,7 +767,10 @@ int refine(Ctx& c, int k, double* Q0, std::vector<double>& D, double tol_rel, do
       break;
     }
   }
-  if (!done) c.S.not_converged += 1;
+  if (!done) {
+    c.S.not_converged += 1;
+    c.S.nc_refine += 1;
+  }
   CK(cudaMemcpyAsync(Qout, Q, sizeof(double) * size_t(n) * mh, cudaMemcpyDeviceToDevice, c.st));
   D.resize(mh);
   return mh;

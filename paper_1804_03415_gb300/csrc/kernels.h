@@ -36,6 +36,10 @@ struct SolverArgs {
   void *r, *p, *q, *z;
   void *ir, *ip, *iq;
   int fp32;        // 1: FP32 instance (matrix val32, FP32 vectors)
+  // mode 0 with fp32 = 1 and b64 != NULL: FP32 CG with FP64 reliable updates;
+  // b64 / x64 (n x m, ld) are the FP64 right-hand side and solution
+  const double* b64;
+  double* x64;
   double tol, itol;
   int maxit, imaxit;
   double* red;         // [4][MT][grid]

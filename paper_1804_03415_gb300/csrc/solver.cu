@@ -309,6 +309,173 @@ __device__ bool cgcg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr) 
   return true;
 }
 
+// FP64 residual of the reliable update: rr32 = (float)(b64 - A x64), partial
+// sums of its square; FP64 SELL SpMV (matrix values in FP64).
+template <int MT>
+__device__ void reliable_residual(const SolverArgs& a, const int* mask, float* r32, double* acc) {
+  const Sell& A = a.A;
+  const int m = a.m;
+  const int64_t ld = a.ld;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t sl = gw; sl < A.nslices; sl += nw) {
+    const int32_t base = A.ptr[sl] + lane, len = A.len[sl];
+    const int32_t row = A.row[sl * 32 + lane];
+    double ax[MT];
+#pragma unroll
+    for (int c = 0; c < MT; ++c) ax[c] = 0.0;
+    for (int32_t k = 0; k < len; ++k) {
+      const double v = A.val[base + k * 32];
+      const int64_t j = A.col[base + k * 32];
+#pragma unroll
+      for (int c = 0; c < MT; ++c)
+        if (c < m && mask[c]) ax[c] = fma(v, a.x64[j + c * ld], ax[c]);
+    }
+    if (row >= 0) {
+#pragma unroll
+      for (int c = 0; c < MT; ++c)
+        if (c < m && mask[c]) {
+          const double rv = a.b64[row + c * ld] - ax[c];
+          r32[row + c * ld] = (float)rv;
+          acc[c] = fma(rv, rv, acc[c]);
+        }
+    }
+  }
+}
+
+// Mode 0, FP32 with FP64 reliable updates (residual replacement): the CG
+// recurrences run in FP32, x accumulates in FP64, and whenever the FP32
+// residual has dropped by 100x since the last replacement -- and before
+// convergence is accepted -- r is replaced by the FP64 residual b - A x.
+// The Krylov recurrence is kept (no restart), so the iteration count stays
+// close to the FP64 one while the SpMV and vector traffic is FP32.
+template <int MT>
+__device__ bool cgcg_rel(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr) {
+  float* const r = (float*)a.r;
+  float* const p = (float*)a.p;
+  float* const w = (float*)a.z;
+  float* const sv = (float*)a.q;
+  const int m = a.m;
+  const int64_t n = a.n, ld = a.ld;
+  float acc[MT];
+  double dacc[MT];
+  // initial residual in FP64 (x64 = x0 or 0)
+  int all1[MT];
+#pragma unroll
+  for (int c = 0; c < MT; ++c) {
+    all1[c] = 1;
+    dacc[c] = 0.0;
+  }
+  if (!a.x0)
+    for (int64_t i = tid; i < n; i += nthr)
+      for (int c = 0; c < m; ++c) a.x64[i + c * ld] = 0.0;
+  if (!grid_sync(a.bar)) return false;
+  reliable_residual<MT>(a, all1, r, dacc);
+  write_partials<MT, double>(a.red, 1, m, dacc, s);
+#pragma unroll
+  for (int c = 0; c < MT; ++c) dacc[c] = 0.0;
+  for (int64_t i = tid; i < n; i += nthr)
+    for (int c = 0; c < m; ++c) dacc[c] = fma(a.b64[i + c * ld], a.b64[i + c * ld], dacc[c]);
+  write_partials<MT, double>(a.red, 0, m, dacc, s);
+  if (!grid_sync(a.bar)) return false;
+  reduce_slot<MT>(a.red, 0, m, s.bn);
+  reduce_slot<MT>(a.red, 1, m, s.rr);
+  if (threadIdx.x < m) {
+    const int c = threadIdx.x;
+    s.bn[c] = sqrt(s.bn[c]);
+    s.act[c] = (s.bn[c] > 0.0) && !(sqrt(s.rr[c]) <= a.tol * s.bn[c]);
+    s.it[c] = 0;
+    s.irn0[c] = sqrt(s.rr[c]);  // norm at the last replacement
+  }
+  __syncthreads();
+  for (int it = 1; it <= a.maxit; ++it) {
+    int any = 0;
+    for (int c = 0; c < m; ++c) any |= s.act[c];
+    if (!any) break;
+#pragma unroll
+    for (int c = 0; c < MT; ++c) acc[c] = 0.0f;
+    spmv_cols<MT, float>(a.A, r, w, ld, m, s.act, r, acc);
+    write_partials<MT, float>(a.red, 0, m, acc, s);
+    if (!grid_sync(a.bar)) return false;
+    reduce_slot<MT>(a.red, 0, m, s.val);
+    if (threadIdx.x < m) {
+      const int c = threadIdx.x;
+      if (s.act[c]) {
+        const double g = s.rr[c], dl = s.val[c];
+        double be = 0.0, den = dl;
+        if (it > 1) {
+          be = g / s.rz[c];
+          den = dl - be * g / s.alpha[c];
+        }
+        if (!(den > 0.0)) {
+          s.act[c] = 0;
+          if (blockIdx.x == 0) atomicExch(a.bar.status, (int)DEV_NOTSPD);
+        }
+        s.rz[c] = g;
+        s.alpha[c] = g / den;
+        s.val2[c] = be;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < MT; ++c) acc[c] = 0.0f;
+    for (int64_t i = tid; i < n; i += nthr)
+      for (int c = 0; c < m; ++c)
+        if (s.act[c]) {
+          const int64_t o = i + c * ld;
+          const bool fresh = (it == 1);
+          const float be = (float)s.val2[c], al = (float)s.alpha[c];
+          const float rv0 = r[o];
+          const float pv = fresh ? rv0 : fmaf(be, p[o], rv0);
+          const float svv = fresh ? w[o] : fmaf(be, sv[o], w[o]);
+          p[o] = pv;
+          sv[o] = svv;
+          a.x64[o] = fma(s.alpha[c], (double)pv, a.x64[o]);
+          const float rv = fmaf(-al, svv, rv0);
+          r[o] = rv;
+          acc[c] = fmaf(rv, rv, acc[c]);
+        }
+    write_partials<MT, float>(a.red, 1, m, acc, s);
+    if (!grid_sync(a.bar)) return false;
+    reduce_slot<MT>(a.red, 1, m, s.val);
+    // replacement needed?  (FP32 residual 100x below the last replaced one, or converged)
+    int need = 0;
+    for (int c = 0; c < m; ++c)
+      if (s.act[c] && (sqrt(s.val[c]) <= 0.01 * s.irn0[c] || sqrt(s.val[c]) <= a.tol * s.bn[c])) need = 1;
+    if (threadIdx.x < m) {
+      const int c = threadIdx.x;
+      if (s.act[c]) {
+        s.it[c] = it;
+        s.rr[c] = s.val[c];
+      }
+    }
+    __syncthreads();
+    if (need) {
+      int msk[MT];
+#pragma unroll
+      for (int c = 0; c < MT; ++c) {
+        msk[c] = (c < m) && s.act[c];
+        dacc[c] = 0.0;
+      }
+      reliable_residual<MT>(a, msk, r, dacc);  // x64 is complete: the barrier above
+      write_partials<MT, double>(a.red, 2, m, dacc, s);
+      if (!grid_sync(a.bar)) return false;
+      reduce_slot<MT>(a.red, 2, m, s.val2);
+      if (threadIdx.x < m) {
+        const int c = threadIdx.x;
+        if (s.act[c]) {
+          s.rr[c] = s.val2[c];
+          s.irn0[c] = sqrt(s.val2[c]);
+          if (sqrt(s.val2[c]) <= a.tol * s.bn[c]) s.act[c] = 0;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  return true;
+}
+
 template <int MT, typename T>
 __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolverArgs a) {
   __shared__ Sh<MT> s;
@@ -323,6 +490,16 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolverArgs a) {
   const int64_t n = a.n, ld = a.ld;
   const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t nthr = int64_t(gridDim.x) * blockDim.x;
+  if constexpr (sizeof(T) == 4) {
+    if (a.mode == 0 && a.b64) {
+      if (!cgcg_rel<MT>(a, s, tid, nthr)) return;
+      if (blockIdx.x == 0 && threadIdx.x < m) {
+        a.it_out[threadIdx.x] = s.it[threadIdx.x];
+        a.conv[threadIdx.x] = s.act[threadIdx.x] ? 0 : 1;
+      }
+      return;
+    }
+  }
   T acc[MT], acc2[MT];
   int all1[MT];
 #pragma unroll
