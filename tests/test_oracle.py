@@ -278,3 +278,57 @@ def test_eig_level_outputs_are_top_of_each_pencil():
         assert np.all(np.diff(mu) <= 1e-12 * mu[0]), "descending"
         tol = 1e-8 * top[0] if k == 0 else D.levels[k - 1].eps
         assert np.abs(np.sort(mu)[::-1] - top).max() <= tol, k
+
+
+# ------------------------------------------------------------------ gradient
+def _loss(A, N, w, k, t):
+    lam, V = np.linalg.eigh(A)
+    v = V[:, k]
+    return float(w @ lam[:N] + 0.5 * np.sum(t * v * v))
+
+
+def test_gradient_dense_vs_finite_differences():
+    """Hellmann-Feynman + first-order eigenvector perturbation against central FD."""
+    from oracle import grad as OG
+    Acsr = W.fd2d(6, seed=77)  # connected, simple spectrum
+    A = Acsr.dense()
+    N, k = 6, 1
+    rng = np.random.default_rng(5)
+    w = rng.uniform(0.5, 1.5, N)
+    t = rng.standard_normal(A.shape[0])
+    lam, V = np.linalg.eigh(A)
+    Gv = np.zeros((A.shape[0], N))
+    Gv[:, k] = t * V[:, k]
+    G = OG.dense_dLdA(A, N, w, Gv)
+    h = 1e-6
+    rows = np.repeat(np.arange(Acsr.n), np.diff(Acsr.rowptr))
+    for e in range(0, Acsr.nnz, 7):
+        r, c = rows[e], Acsr.col[e]
+        E = np.zeros_like(A)
+        E[r, c] = 1.0
+        E[c, r] = 1.0
+        fd = (_loss(A + h * E, N, w, k, t) - _loss(A - h * E, N, w, k, t)) / (2 * h)
+        an = G[r, c] + (G[c, r] if r != c else 0.0)
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (r, c, fd, an)
+
+
+def test_gradient_block_plus_complement_matches_dense():
+    """The N-pair form (in-block terms + projected CG on the complement) equals the full closed form."""
+    from oracle import grad as OG
+    Acsr = W.fd2d(8, seed=78)
+    A = Acsr.dense()
+    N, k = 8, 2
+    rng = np.random.default_rng(6)
+    gl = rng.uniform(0.5, 1.5, N)
+    lam, V = np.linalg.eigh(A)
+    t = rng.standard_normal(A.shape[0])
+    Gv = np.zeros((A.shape[0], N))
+    Gv[:, k] = t * V[:, k]
+    Gd = OG.dense_dLdA(A, N, gl, Gv)
+    rows = np.repeat(np.arange(Acsr.n), np.diff(Acsr.rowptr))
+    g = OG.dLdvals(Acsr, lam[:N], V[:, :N], gl, Gv, tol=1e-13)
+    assert np.allclose(g, Gd[rows, Acsr.col], atol=1e-9 * np.abs(Gd).max())
+    # eigenvalue-only loss: G_rc = sum_i gl_i v_i(r) v_i(c), no solves
+    g0 = OG.dLdvals(Acsr, lam[:N], V[:, :N], gl, None)
+    G0 = (V[:, :N] * gl) @ V[:, :N].T
+    assert np.allclose(g0, G0[rows, Acsr.col], atol=1e-13)
