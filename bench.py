@@ -8,7 +8,14 @@ outside the timed region (its time is reported as build_s); each timed step
 is one full eigensolve with the matrix and levels resident in HBM.  L2 is
 flushed (a 512 MB write) before every timed step.
 
+``--precision`` picks the timed form (fp64 = MMD_FP64, mixed = MMD_MIXED:
+FP32 PCG on the coarse levels inside FP64 refinement, mixed_all =
+MMD_MIXED_ALL: FP32 level-0 CG with FP64 reliable updates as well); the other
+of fp64 / mixed is timed after it on the same handle and reported under
+``compare``.
+
 Also reported:
+  * t_level_ms -- wall time per level of the timed step;
   * e2e     -- the same metric through the public API with host buffers:
                mmd_build from a host CSR + eig_leftmost into host outputs;
   * spmv    -- standalone FP64 CSR SpMV GB/s on the 128^3 7-point operator
@@ -40,6 +47,7 @@ WORKLOAD = {"workload": "torus_knn_200k", "n": 200000, "k": 10, "N": 500, "tol":
             "matrix": "torus kNN Laplacian + 1e-6 I, FP64 CSR", "l2": "flushed before each step"}
 SAMPLE = {"npts": 5000, "N": 20, "tol": 1e-8}  # bounded oracle sample of the same workload kind
 FALLBACK_HBM = 6800.0
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_all": 2}  # MMD_FP64, MMD_MIXED, MMD_MIXED_ALL
 
 
 def peaks():
@@ -154,29 +162,48 @@ def gpu_arm(args, rank, world):
     V = torch.zeros((N, A.n), dtype=torch.float64, device="cuda")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def step(profile):
-        return h.eig_leftmost(N, tol, out=(lam, V), allow_noconv=True, stream=sptr, profile=profile)[2]
+    prec = PRECISIONS[args.precision]
+
+    def step(profile, precision=prec):
+        return h.eig_leftmost(N, tol, out=(lam, V), allow_noconv=True, stream=sptr, profile=profile,
+                              precision=precision)[2]
+
+    def timed(steps, precision):
+        ev, sts = [], []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sts.append(step(1, precision))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ev.append(e0.elapsed_time(e1))
+        return ev, sts
 
     for _ in range(args.warmup):
         step(0)
     dist_barrier(world)
     clk = ClockSampler(dev)
     clk.start()
-    ev = []
-    stats = []
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        stats.append(step(1))
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ev.append(e0.elapsed_time(e1))
+    ev, stats = timed(args.steps, prec)
     clocks = clk.stop()
     ms_local = float(np.sum(ev))
     ms = dist_max(ms_local, world)
     value = world * N * args.steps / (ms / 1e3)
+    # the other precision on the same handle (one untimed warm-up step first)
+    compare = None
+    if not args.no_compare:
+        other = "fp64" if args.precision != "fp64" else "mixed"
+        step(0, PRECISIONS[other])
+        dist_barrier(world)
+        ev2, st2 = timed(args.steps, PRECISIONS[other])
+        ms2 = dist_max(float(np.sum(ev2)), world)
+        compare = {"precision": other, "value": world * N * args.steps / (ms2 / 1e3), "unit": "eigenpairs/s",
+                   "ms_per_step": ms2 / args.steps,
+                   "residual": {"max_rel": st2[-1]["max_rel_residual"], "n_converged": st2[-1]["n_converged"]},
+                   "t_level_ms": st2[-1]["t_level_ms"], "pcg_iters": st2[-1]["pcg_iters"],
+                   "refine_pcg_iters": st2[-1]["refine_pcg_iters"]}
     # end to end: host CSR in, host outputs out, through the public API
     e2e_times = []
     lam_h = np.zeros(N)
@@ -185,7 +212,7 @@ def gpu_arm(args, rank, world):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h2 = G.MMD(A.rowptr, A.col, A.val)
-        st2 = G.eig_opts(stream=sptr)
+        st2 = G.eig_opts(stream=sptr, precision=prec)
         import ctypes as C
 
         s2 = G._lib.mmd_eig_stats()
@@ -209,10 +236,13 @@ def gpu_arm(args, rank, world):
     out = {
         "metric": "leftmost eigenpairs/sec to residual 1e-8", "value": value, "unit": "eigenpairs/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(WORKLOAD, precision="fp64", parallelism=f"replicas{world}"),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": dict(WORKLOAD, precision=args.precision, parallelism=f"replicas{world}"),
         "build_s": build_s,
         "residual": {"max_rel": st0["max_rel_residual"], "n_converged": st0["n_converged"]},
+        "t_level_ms": st0["t_level_ms"],
+        "compare": compare,
         "counters": {k: st0[k] for k in ("op_calls", "pcg_iters", "inner_iters", "b_iters", "refine_pcg_iters",
                                          "restarts", "lanczos_steps", "refine_iters", "n_levels")},
         "e2e": {"value": world * N / e2e_s, "unit": "eigenpairs/s", "h2d_bytes_per_step": h2d,
@@ -288,7 +318,8 @@ def dist_max(v, world):
 
 def kernel_case(which: str):
     """Small fixed launches for ncu captures: 'op' = three Operator OP solves on
-    level 0 of the torus 200k workload (one solver launch each), 'spmv' = three
+    level 0 of the torus 200k workload (one solver launch each), 'block' =
+    three 8-column OP solves there (the refinement's tile), 'spmv' = three
     FP64 SpMVs on the 128^3 operator."""
     import torch
 
@@ -302,6 +333,13 @@ def kernel_case(which: str):
         y = torch.empty_like(x)
         its = [h.level_op(0, x, y, 1e-6) for _ in range(3)]
         print(json.dumps({"kernel_case": "op", "iters": its}))
+    elif which == "block":
+        A = W.torus_knn(WORKLOAD["n"], k=WORKLOAD["k"], seed=W.BASE_SEED + 1)
+        h = G.MMD(A.rowptr, A.col, A.val, k_max=1)
+        X = torch.rand((8, A.n), dtype=torch.float64, device="cuda")
+        Y = torch.empty_like(X)
+        its = [h.level_op_block(0, X, Y, 1e-6) for _ in range(3)]
+        print(json.dumps({"kernel_case": "block", "iters": its}))
     else:
         A = W.fd3d(128, seed=W.BASE_SEED + 2)
         h = G.MMD(A.rowptr, A.col, A.val, k_max=0)
@@ -322,7 +360,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--oracle-worker", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel-case", choices=["op", "spmv"], default=None)
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp64")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other precision")
+    ap.add_argument("--kernel-case", choices=["op", "block", "spmv"], default=None)
     args = ap.parse_args()
     if args.oracle_worker:
         oracle_sample_worker(args.oracle_worker)

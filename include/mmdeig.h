@@ -50,8 +50,11 @@ extern "C" {
 #define MMD_ENOMEM (-6)   /* host or device allocation failed */
 
 /* precision modes of eig_leftmost */
-#define MMD_FP64 0  /* every step in FP64 */
-#define MMD_MIXED 1 /* FP32 inner solves, FP64 outer residual and refinement */
+#define MMD_FP64 0      /* every step in FP64 */
+#define MMD_MIXED 1     /* coarse levels k >= 1: FP32 PCG inside FP64 iterative
+                           refinement; level 0 and all dense work in FP64 */
+#define MMD_MIXED_ALL 2 /* as MMD_MIXED, and level-0 CG with FP32 recurrences and
+                           FP64 reliable updates (for kappa(A) well below 1/u_32) */
 
 typedef struct mmd_handle mmd_handle;
 
@@ -84,7 +87,7 @@ typedef struct {
   double beta;         /* extension threshold mu_ex^(k) = beta eps_k (default 1) */
   int d;               /* searching step, 0 = min(N^(k)/10, N/10) clamped to >= 1 */
   int c_r;             /* restart factor: p = c_r * d shifts (default 1) */
-  int precision;       /* MMD_FP64 or MMD_MIXED */
+  int precision;       /* MMD_FP64, MMD_MIXED or MMD_MIXED_ALL */
   int max_cg_iter;     /* cap per CG/PCG call (default 20000) */
   int max_restarts;    /* cap per convergence loop (default 400) */
   int max_refine_iter; /* cap of Algorithm 5 iterations (default 100) */
@@ -114,6 +117,8 @@ typedef struct {
   int64_t pcg_launches;
   double pcg_ms;        /* sum of event-timed durations */
   double pcg_bytes;     /* algorithmic bytes moved by those launches */
+  int64_t fp64_finishes; /* MMD_MIXED_ALL: level-0 CG columns FP32 left unconverged, finished in FP64 */
+  double t_level_ms[16]; /* wall time per level k (coarsest solve; refinement + extension) */
 } mmd_eig_stats;
 
 /* Read-only view of level k (1 <= k <= K) of a handle; host pointers owned by
@@ -174,17 +179,54 @@ int eig_leftmost(mmd_handle* h, int N, double tol, const mmd_eig_opts* opts,
                  double* lambda, double* V, int outputs_on_device,
                  mmd_eig_stats* stats);
 
+/* eig_leftmost on `count` independent problems at once (the data-parallel
+ * use of Algorithm 6: one decomposition per graph).  hs[i], N[i], lambda[i],
+ * V[i] and stats[i] (stats may be NULL) are those of problem i; tol and opts
+ * are shared (opts->stream is ignored).  The problems run concurrently on
+ * `streams` non-blocking CUDA streams (<= 0: 8), one host thread per stream,
+ * problem i on stream i mod streams.  Each stream's cooperative solver
+ * launches use at most (SM count / streams) blocks, so the concurrent grids
+ * are co-resident.  The handles must be distinct.  Returns MMD_OK, or the first failing problem's code (all
+ * problems are still attempted; mmd_last_error names the problem). */
+int eig_leftmost_batched(mmd_handle* const* hs, int count, const int* N, double tol, const mmd_eig_opts* opts,
+                         double* const* lambda, double* const* V, int outputs_on_device,
+                         mmd_eig_stats* stats, int streams);
+
+/* Gradient of a loss L(lambda, V) of the last eig_leftmost result of h with
+ * respect to the stored values of the input CSR (not in the paper; the
+ * adjoint of the solver's output).  With (lambda_i, v_i), i < N, the pairs
+ * returned by that call, gl = dL/dlambda (N) and Gv = dL/dV (n x N,
+ * column-major, NULL when L depends on lambda only):
+ *   dL/dval_e = sum_i [gl_i v_i(r_e) + y_i(r_e)] v_i(c_e),
+ *   y_i = -(A - lambda_i I)^+ g_i  (first-order eigenvector perturbation),
+ * where y_i = in-block terms sum_{j != i} v_j (v_j^T g_i)/(lambda_i - lambda_j)
+ * plus the solution z of (A - lambda_i I) z = -(I - V V^T) g_i on the
+ * complement of the block (conjugate gradients; needs lambda_i < lambda_{N+1}).
+ * e runs over the stored entries in the input's CSR order; a symmetric pair
+ * (r, c), (c, r) receives its two derivatives separately.  Assumes simple
+ * eigenvalues for the pairs with nonzero Gv columns.  Inputs and the output
+ * (nnz doubles) are device memory when the flags are 1.  Errors: MMD_EINVAL
+ * (no previous result), MMD_ENOTSPD (lambda_i not below the complement). */
+int eig_grad(mmd_handle* h, const double* dL_dlambda, const double* dL_dV, int inputs_on_device, double* dL_dvals,
+             int output_on_device, const mmd_eig_opts* opts);
+
 /* Level operators on device vectors of level k, in the natural (build) order
  * of that level, for tests and kernel benchmarks.
  * mmd_level_spmv: y = A^(k) x (which = 0) or M^(k) x (which = 1, k >= 1).
  * mmd_level_op: y = OP(x) = pcg(A^(k), M^(k) x, M^(k), 0, tol) (the Operator
  *   OP box after Algorithm 3); k = 0 uses M = I (plain CG).  iters may be NULL.
+ * mmd_level_op_block: Y = OP(X) for m columns (n_k x m, column-major), the
+ *   warm-start-free form of the refinement's multi-right-hand-side PCG
+ *   (Algorithm 5), 8 columns per solver launch; precision as in
+ *   mmd_eig_opts; iters (m entries) may be NULL.
  * mmd_level_bsolve: x = U g where g = CG(B^(k), U^T M^(k-1) q, tol) and
  *   B^(k) = U^(k)^T A^(k-1) U^(k) (Algorithm 5, first loop); q and x are
  *   level-(k-1) vectors, 1 <= k <= K. */
 int mmd_level_spmv(mmd_handle* h, int k, int which, const double* x, double* y, void* stream);
 int mmd_level_op(mmd_handle* h, int k, const double* x, double* y, double tol, int max_iter,
                  int64_t* iters, void* stream);
+int mmd_level_op_block(mmd_handle* h, int k, int m, const double* X, double* Y, double tol, int max_iter,
+                       int64_t* iters, int precision, void* stream);
 int mmd_level_bsolve(mmd_handle* h, int k, const double* q, double* x, double tol, int max_iter,
                      int64_t* iters, void* stream);
 

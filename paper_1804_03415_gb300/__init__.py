@@ -16,7 +16,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import MMD_FP64, MMD_MIXED, MMDError  # noqa: F401
+from ._lib import MMD_FP64, MMD_MIXED, MMD_MIXED_ALL, MMDError  # noqa: F401
 
 
 def build_opts(**kw) -> _lib.mmd_build_opts:
@@ -116,6 +116,14 @@ class MMD:
                    "mmd_level_op")
         return it.value
 
+    def level_op_block(self, k, X, Y, tol, max_iter=20000, precision=MMD_FP64, stream=0):
+        """Y = OP(X) column by column; X, Y: CUDA float64 tensors (m, n_k), one row per column."""
+        m = X.shape[0]
+        its = (C.c_int64 * m)()
+        _lib.check(self._lib.mmd_level_op_block(self.h, k, m, X.data_ptr(), Y.data_ptr(), tol, max_iter, its,
+                                                precision, stream), "mmd_level_op_block")
+        return list(its)
+
     def level_bsolve(self, k, q, x, tol, max_iter=20000, stream=0) -> int:
         it = C.c_int64(0)
         _lib.check(self._lib.mmd_level_bsolve(self.h, k, q.data_ptr(), x.data_ptr(), tol, max_iter, C.byref(it),
@@ -138,3 +146,83 @@ class MMD:
         if rc != _lib.MMD_OK and not (allow_noconv and rc == _lib.MMD_ENOCONV):
             _lib.check(rc, "eig_leftmost")
         return res[0], res[1], st.as_dict()
+
+    def eig_grad(self, dL_dlambda, dL_dV=None, out=None, **opts):
+        """dL/dval per stored CSR entry for the last eig_leftmost result.
+
+        Host numpy inputs -> host numpy output; CUDA tensors -> CUDA tensor
+        (or ``out``)."""
+        o = eig_opts(**opts)
+        if hasattr(dL_dlambda, "data_ptr"):
+            import torch
+
+            g = out if out is not None else torch.zeros(self.nnz, dtype=torch.float64, device=dL_dlambda.device)
+            gv = dL_dV.contiguous() if dL_dV is not None else None
+            rc = self._lib.eig_grad(self.h, dL_dlambda.data_ptr(), gv.data_ptr() if gv is not None else None, 1,
+                                    g.data_ptr(), 1, C.byref(o))
+            _lib.check(rc, "eig_grad")
+            return g
+        gl = np.ascontiguousarray(dL_dlambda, dtype=np.float64)
+        g = np.zeros(self.nnz)
+        gv = None
+        if dL_dV is not None:
+            gv = np.ascontiguousarray(np.asarray(dL_dV, dtype=np.float64).T)  # (N, n) rows = columns of n x N
+        rc = self._lib.eig_grad(self.h, gl.ctypes.data, gv.ctypes.data if gv is not None else None, 0,
+                                g.ctypes.data, 0, C.byref(o))
+        _lib.check(rc, "eig_grad")
+        return g
+
+
+def eig_leftmost_batched(handles, N, tol: float, streams: int = 8, **opts):
+    """N[i] smallest eigenpairs of each handle's matrix, the problems solved
+    concurrently on ``streams`` CUDA streams (eig_leftmost_batched).
+
+    ``N``: int or one int per handle.  Returns lists (lam_i, V_i, stats_i),
+    host numpy arrays."""
+    lib = _lib.load()
+    cnt = len(handles)
+    Ns = [int(N)] * cnt if np.isscalar(N) else [int(x) for x in N]
+    if len(Ns) != cnt:
+        raise ValueError("one N per handle")
+    o = eig_opts(**opts)
+    lams = [np.zeros(Ns[i]) for i in range(cnt)]
+    Vs = [np.zeros((Ns[i], handles[i].n)) for i in range(cnt)]
+    hs = (C.c_void_p * cnt)(*[h.h.value for h in handles])
+    na = (C.c_int * cnt)(*Ns)
+    lp = (C.c_void_p * cnt)(*[a.ctypes.data for a in lams])
+    vp = (C.c_void_p * cnt)(*[a.ctypes.data for a in Vs])
+    st = (_lib.mmd_eig_stats * cnt)()
+    rc = lib.eig_leftmost_batched(hs, cnt, na, tol, C.byref(o), lp, vp, 0, st, streams)
+    _lib.check(rc, "eig_leftmost_batched")
+    return [(lams[i], Vs[i].T, st[i].as_dict()) for i in range(cnt)]
+
+
+def eigsh_leftmost(rowptr, col, val, N: int, tol: float = 1e-8, build=None, **opts):
+    """Differentiable leftmost eigenpairs of the symmetric CSR matrix (rowptr, col, val).
+
+    ``val`` is a CUDA float64 tensor (the values that receive gradients);
+    rowptr / col are int32 tensors.  Returns (lambda (N,), V (n, N)).  The
+    forward pass is eig_leftmost, the backward pass eig_grad.
+    """
+    import torch
+
+    class _Eig(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, v):
+            h = MMD(rowptr, col, v, **(build or {}))
+            n = rowptr.numel() - 1
+            lam = torch.zeros(N, dtype=torch.float64, device=v.device)
+            Vt = torch.zeros((N, n), dtype=torch.float64, device=v.device)
+            h.eig_leftmost(N, tol, out=(lam, Vt), **opts)
+            ctx.h = h
+            return lam, Vt.T
+
+        @staticmethod
+        def backward(ctx, glam, gV):
+            gl = glam if glam is not None else torch.zeros(N, dtype=torch.float64, device=glam.device)
+            gv = gV.T.contiguous() if gV is not None else None
+            g = ctx.h.eig_grad(gl.contiguous(), gv)
+            ctx.h.close()
+            return g
+
+    return _Eig.apply(val)

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmmdeig.so")
 
 MMD_OK, MMD_EINVAL, MMD_ENOTSPD, MMD_ENOCONV, MMD_ETIMEOUT, MMD_ECUDA, MMD_ENOMEM = 0, -1, -2, -3, -4, -5, -6
-MMD_FP64, MMD_MIXED = 0, 1
+MMD_FP64, MMD_MIXED, MMD_MIXED_ALL = 0, 1, 2
 
 i32p = C.POINTER(C.c_int32)
 f64p = C.POINTER(C.c_double)
@@ -45,10 +45,13 @@ class mmd_eig_stats(C.Structure):
                 ("nc_restart", C.c_int64), ("nc_refine", C.c_int64), ("kernel_launches", C.c_int64),
                 ("n_levels", C.c_int), ("n_converged", C.c_int), ("norm_A", C.c_double),
                 ("max_rel_residual", C.c_double), ("mu1", C.c_double), ("t_total_ms", C.c_double),
-                ("pcg_launches", C.c_int64), ("pcg_ms", C.c_double), ("pcg_bytes", C.c_double)]
+                ("pcg_launches", C.c_int64), ("pcg_ms", C.c_double), ("pcg_bytes", C.c_double),
+                ("fp64_finishes", C.c_int64), ("t_level_ms", C.c_double * 16)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["t_level_ms"] = [float(v) for v in self.t_level_ms[: max(self.n_levels, 0)]]
+        return d
 
 
 class mmd_level_view(C.Structure):
@@ -69,15 +72,22 @@ SIGNATURES = {
     "mmd_level_info": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(mmd_level_view)]),
     "eig_leftmost": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(mmd_eig_opts), C.c_void_p, C.c_void_p,
                                C.c_int, C.POINTER(mmd_eig_stats)]),
+    "eig_leftmost_batched": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_double, C.POINTER(mmd_eig_opts),
+                                       C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "eig_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
+                           C.POINTER(mmd_eig_opts)]),
     "mmd_level_spmv": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mmd_level_op": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                C.POINTER(C.c_int64), C.c_void_p]),
+    "mmd_level_op_block": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                                     C.c_void_p, C.c_int, C.c_void_p]),
     "mmd_level_bsolve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                    C.POINTER(C.c_int64), C.c_void_p]),
     "mmd_free": (None, [C.c_void_p]),
     "mmd_strerror": (C.c_char_p, [C.c_int]),
     "mmd_last_error": (C.c_char_p, []),
 }
+
 
 _lib = None
 

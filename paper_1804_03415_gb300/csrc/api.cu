@@ -6,6 +6,8 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
+#include <vector>
 
 #include "driver.h"
 #include "kernels.h"
@@ -223,6 +225,10 @@ void free_device(mmd_handle* h) {
     cudaFree(L.d_iperm);
   }
   h->dl.clear();
+  cudaFree(h->d_in_rowptr);
+  cudaFree(h->d_in_col);
+  h->d_in_rowptr = nullptr;
+  h->d_in_col = nullptr;
   free_workspace(h);
 }
 
@@ -400,6 +406,16 @@ int mmd_level_op(mmd_handle* h, int k, const double* x, double* y, double tol, i
   return level_op(h, k, x, y, tol, max_iter, iters, (cudaStream_t)stream);
 }
 
+int mmd_level_op_block(mmd_handle* h, int k, int m, const double* X, double* Y, double tol, int max_iter,
+                       int64_t* iters, int precision, void* stream) {
+  if (!h || !h->on_device || k < 0 || k > (int)h->levels.size() || m < 1 || !X || !Y || !(tol > 0) ||
+      max_iter < 1 || (precision != MMD_FP64 && precision != MMD_MIXED && precision != MMD_MIXED_ALL)) {
+    set_error("mmd_level_op_block: bad arguments");
+    return MMD_EINVAL;
+  }
+  return level_op_block(h, k, m, X, Y, tol, max_iter, iters, precision, (cudaStream_t)stream);
+}
+
 int mmd_level_bsolve(mmd_handle* h, int k, const double* q, double* x, double tol, int max_iter, int64_t* iters,
                      void* stream) {
   if (!h || !h->on_device || k < 1 || k > (int)h->levels.size() || !q || !x || !(tol > 0) || max_iter < 1) {
@@ -423,11 +439,79 @@ int eig_leftmost(mmd_handle* h, int N, double tol, const mmd_eig_opts* opts, dou
   mmd_default_eig_opts(&o);
   if (opts) o = *opts;
   if (!(o.alpha > 0) || !(o.beta > 0) || o.c_r < 1 || o.max_cg_iter < 1 || o.max_restarts < 1 ||
-      o.max_refine_iter < 1 || !(o.timeout_s > 0) || (o.precision != MMD_FP64 && o.precision != MMD_MIXED)) {
+      o.max_refine_iter < 1 || !(o.timeout_s > 0) || (o.precision != MMD_FP64 && o.precision != MMD_MIXED && o.precision != MMD_MIXED_ALL)) {
     set_error("eig_leftmost: invalid options");
     return MMD_EINVAL;
   }
   return run_eig(h, N, tol, o, lambda, V, outputs_on_device, stats);
+}
+
+int eig_leftmost_batched(mmd_handle* const* hs, int count, const int* N, double tol, const mmd_eig_opts* opts,
+                         double* const* lambda, double* const* V, int outputs_on_device, mmd_eig_stats* stats,
+                         int streams) {
+  if (!hs || count < 1 || !N || !lambda || !V || !(tol > 0)) {
+    set_error("eig_leftmost_batched: bad arguments");
+    return MMD_EINVAL;
+  }
+  for (int i = 0; i < count; ++i)
+    if (!hs[i] || !hs[i]->on_device || N[i] < 1 || N[i] > hs[i]->A0.nrows || !lambda[i] || !V[i]) {
+      set_error("eig_leftmost_batched: problem " + std::to_string(i) + " has a bad handle, N or output");
+      return MMD_EINVAL;
+    }
+  mmd_eig_opts o;
+  mmd_default_eig_opts(&o);
+  if (opts) o = *opts;
+  const int ns = std::max(1, std::min(count, streams > 0 ? streams : 8));
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // the streams' cooperative grids (one block per SM each) share the SMs
+  const int cap = std::max(1, nsm / ns);
+  std::vector<cudaStream_t> st(ns, nullptr);
+  for (int t = 0; t < ns; ++t)
+    if (cudaStreamCreateWithFlags(&st[t], cudaStreamNonBlocking) != cudaSuccess) {
+      for (int u = 0; u < t; ++u) cudaStreamDestroy(st[u]);
+      set_error("eig_leftmost_batched: stream creation failed");
+      return MMD_ECUDA;
+    }
+  std::vector<int> rcs(count, MMD_OK);
+  std::vector<std::string> msgs(count);
+  std::vector<std::thread> th;
+  for (int t = 0; t < ns; ++t)
+    th.emplace_back([&, t]() {
+      cudaSetDevice(dev);
+      set_coop_grid_cap(cap);
+      mmd_eig_opts ot = o;
+      ot.stream = st[t];
+      for (int i = t; i < count; i += ns) {
+        rcs[i] = run_eig(hs[i], N[i], tol, ot, lambda[i], V[i], outputs_on_device, stats ? &stats[i] : nullptr);
+        if (rcs[i] != MMD_OK) msgs[i] = mmd_last_error();
+      }
+    });
+  for (auto& x : th) x.join();
+  for (int t = 0; t < ns; ++t) cudaStreamDestroy(st[t]);
+  for (int i = 0; i < count; ++i)
+    if (rcs[i] != MMD_OK) {
+      set_error("eig_leftmost_batched: problem " + std::to_string(i) + ": " + msgs[i]);
+      return rcs[i];
+    }
+  return MMD_OK;
+}
+
+int eig_grad(mmd_handle* h, const double* dL_dlambda, const double* dL_dV, int inputs_on_device, double* dL_dvals,
+             int output_on_device, const mmd_eig_opts* opts) {
+  if (!h || !h->on_device || !dL_dlambda || !dL_dvals) {
+    set_error("eig_grad: needs a device handle, dL_dlambda and dL_dvals");
+    return MMD_EINVAL;
+  }
+  if (h->last_N < 1) {
+    set_error("eig_grad: call eig_leftmost on this handle first");
+    return MMD_EINVAL;
+  }
+  mmd_eig_opts o;
+  mmd_default_eig_opts(&o);
+  if (opts) o = *opts;
+  return run_grad(h, dL_dlambda, dL_dV, inputs_on_device, dL_dvals, output_on_device, o);
 }
 
 }  // extern "C"

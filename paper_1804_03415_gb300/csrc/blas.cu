@@ -468,3 +468,31 @@ void k_residuals(const Sell& A, int64_t n, const double* V, int64_t ld, int m, c
 }
 
 }  // namespace mmd
+
+namespace mmd {
+namespace {
+// G[e] = sum_i U(r_e, i) V(c_e, i) for the stored entries e of a CSR pattern
+// (sampled dense-dense product); one warp per row, one lane per entry.
+__global__ void sddmm_kernel(const int32_t* rp, const int32_t* ci, int64_t n, const double* U, const double* V,
+                             int64_t ld, int N, double* G) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < n;
+       r += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+    for (int32_t e = rp[r] + lane; e < rp[r + 1]; e += 32) {
+      const int64_t c = ci[e];
+      double s = 0.0;
+      for (int i = 0; i < N; ++i) s = fma(U[r + i * ld], V[c + i * ld], s);
+      G[e] = s;
+    }
+  }
+}
+}  // namespace
+
+void k_sddmm(const int32_t* rp, const int32_t* ci, int64_t n, const double* U, const double* V, int64_t ld, int N,
+             double* G, cudaStream_t st) {
+  int64_t b = (n * 32 + 255) / 256;
+  if (b > 152 * 64) b = 152 * 64;
+  if (b < 1) b = 1;
+  sddmm_kernel<<<(int)b, 256, 0, st>>>(rp, ci, n, U, V, ld, N, G);
+}
+}  // namespace mmd

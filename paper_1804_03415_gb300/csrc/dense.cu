@@ -11,14 +11,16 @@
 //   * tridiagonal eigenvectors: inverse iteration with a partially pivoted
 //     tridiagonal LU, one thread per cluster of close eigenvalues, modified
 //     Gram-Schmidt inside a cluster (Wilkinson's inverse iteration);
-//   * p shifted QR sweeps (implicit bulge chases, Golub and Van Loan Alg.
-//     8.3.2): the p bulges move down the matrix together, bulge j three
-//     positions behind bulge j-1, so one step of the schedule performs up to
-//     p independent rotations; the rotations are recorded and applied to Q by
-//     many blocks, one row of Q per thread;
+//   * p explicitly shifted QR steps, one Givens sweep each: the p sweeps
+//     move down the matrix together, sweep j three positions behind sweep
+//     j-1, so one step of the schedule performs up to p independent
+//     rotations; the rotations are recorded and applied to Q by many
+//     blocks, one row of Q per thread;
 //   * dense symmetric eigenproblems: Householder tridiagonalisation on one
 //     block, then the two tridiagonal kernels and a parallel back-transform.
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include "dev_common.cuh"
 #include "kernels.h"
@@ -198,19 +200,29 @@ __global__ void tri_inviter_kernel(const double* d, const double* e, int n, cons
 }
 
 // ------------------------------------------------------------ QR sweeps
-// One block.  sd/se: the tridiagonal in shared memory.  Rotation r of step s
-// for shift j acts on positions (k, k+1), k = s - 3 j; recorded to rc/rs
-// [step * p + j] (c = 1, s = 0 for inactive slots).
+// p explicitly shifted QR steps T - s_j I = Q_j R_j, T <- R_j Q_j + s_j I
+// (Algorithm 2), each one Givens sweep down the tridiagonal.  With exact
+// shifts the explicit step keeps the deflation that the implicit bulge chase
+// loses in floating point.  One block; sd/se hold T in shared memory and
+// shift j works at position k = step - 3 j, so shift j reads only entries
+// that shift j - 1 has finished (d_{k+1} at position k + 1, e_{k+1} at k + 2).
+// Per position: rotation k combines the partly reduced row k, (x, y) in
+// columns (k, k+1), with row k+1 of T - s I; then
+//   d'_k = c_{k-1} c_k R_kk + s_k R_{k,k+1} + s,   e'_{k-1} = s_{k-1} R_kk,
+// and at k = n-2 also the last row (d'_{n-1}, e'_{n-2}).  Rotation (c, s) of
+// step t for shift j is recorded at rc/rs[t * p + j] (c = 1, s = 0 when idle).
 __global__ void tri_chase_kernel(double* d, double* e, int n, const double* sh, int p, double* rc, double* rs,
                                  int nsteps) {
   extern __shared__ double smem[];
   double* sd = smem;
   double* se = smem + n;
-  double* sx = se + n;        // carried x per shift
-  double* sz = sx + p;        // carried bulge per shift
+  double* sx = se + n;   // carried R row: diagonal candidate
+  double* sy = sx + p;   //                superdiagonal candidate
+  double* scp = sy + p;  // previous rotation of this shift
+  double* ssp = scp + p;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     sd[k] = d[k];
-    if (k < n - 1) se[k] = e[k];
+    se[k] = (k < n - 1) ? e[k] : 0.0;
   }
   __syncthreads();
   for (int step = 0; step < nsteps; ++step) {
@@ -218,30 +230,37 @@ __global__ void tri_chase_kernel(double* d, double* e, int n, const double* sh, 
       const int k = step - 3 * j;
       double c = 1.0, s = 0.0;
       if (k >= 0 && k <= n - 2) {
-        double x, z;
+        const double sj = sh[j];
+        double x, y, cp, sp;
         if (k == 0) {
-          x = sd[0] - sh[j];
-          z = se[0];
+          x = sd[0] - sj;
+          y = se[0];
+          cp = 1.0;
+          sp = 0.0;
         } else {
           x = sx[j];
-          z = sz[j];
+          y = sy[j];
+          cp = scp[j];
+          sp = ssp[j];
         }
-        const double r = hypot(x, z);
+        const double ek = se[k], d1 = sd[k + 1] - sj, e1 = (k + 1 <= n - 2) ? se[k + 1] : 0.0;
+        const double r = hypot(x, ek);
         if (r > 0) {
           c = x / r;
-          s = z / r;
+          s = ek / r;
         }
-        if (k > 0) se[k - 1] = r;
-        const double a = sd[k], b = se[k], dd = sd[k + 1];
-        const double cs = c * s, cc = c * c, ss = s * s;
-        sd[k] = cc * a + 2 * cs * b + ss * dd;
-        sd[k + 1] = ss * a - 2 * cs * b + cc * dd;
-        se[k] = cs * (dd - a) + (cc - ss) * b;
-        if (k < n - 2) {
-          sz[j] = s * se[k + 1];
-          se[k + 1] = c * se[k + 1];
+        const double rk1 = c * y + s * d1;
+        const double xn = -s * y + c * d1;
+        sd[k] = cp * c * r + s * rk1 + sj;
+        if (k >= 1) se[k - 1] = sp * r;
+        if (k == n - 2) {
+          sd[n - 1] = c * xn + sj;
+          se[n - 2] = s * xn;
         }
-        sx[j] = se[k];
+        sx[j] = xn;
+        sy[j] = c * e1;
+        scp[j] = c;
+        ssp[j] = s;
       }
       rc[size_t(step) * p + j] = c;
       rs[size_t(step) * p + j] = s;
@@ -754,7 +773,8 @@ struct TriScratch {
   double* work;    // 5 n^2
   int* iwork;      // n^2
 };
-static TriScratch g_tri = {};
+// one per host thread: concurrent solves (eig_leftmost_batched) use their own
+static thread_local TriScratch g_tri = {};
 
 void set_tri_scratch(double* bounds, double* e2, int* cstart, int* ncl, double* work, int* iwork) {
   g_tri = {bounds, e2, cstart, ncl, work, iwork};
@@ -776,11 +796,10 @@ void k_tri_eigvecs(const double* d, const double* e, int n, const double* w, dou
 
 void k_tri_ql(const double* d, const double* e, int n, double* w, double* Z, int ldz, double* zl, int* status,
               cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
     cudaFuncSetAttribute(tri_ql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  });
   const size_t smem = sizeof(double) * 4 * size_t(n);
   tri_ql_kernel<<<1, 256, smem, st>>>(d, e, n, w, Z, ldz, zl, status);
 }
@@ -789,12 +808,11 @@ void k_tri_qr_sweeps(double* d, double* e, int n, const double* sh, int p, doubl
   const int nsteps = (n - 1) + 3 * (p - 1);
   double* rc = g_tri.work;
   double* rs = g_tri.work + size_t(nsteps) * p;
-  const size_t smem = sizeof(double) * (2 * size_t(n) + 2 * size_t(p));
-  static bool attr_set = false;
-  if (!attr_set) {
+  const size_t smem = sizeof(double) * (2 * size_t(n) + 4 * size_t(p));
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
     cudaFuncSetAttribute(tri_chase_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  });
   tri_chase_kernel<<<1, 512, smem, st>>>(d, e, n, sh, p, rc, rs, nsteps);
   tri_apply_rot_kernel<<<(n + 7) / 8, 8, 0, st>>>(n, p, nsteps, rc, rs, Q, ldq);
 }
@@ -819,6 +837,10 @@ int k_syev(double* A, int lda, int n, double* w, double* Z, int ldz, double* wor
   return 0;
 }
 
+static thread_local int g_coop_cap = 0;
+void set_coop_grid_cap(int blocks) { g_coop_cap = blocks; }
+int coop_grid_cap() { return g_coop_cap; }
+
 int jacobi_max_grid() {
   int dev = 0, nsm = 0, nb = 0;
   cudaGetDevice(&dev);
@@ -838,9 +860,9 @@ cudaError_t k_syev_jacobi(double* S, int m, double* V, double* work, int* iwork,
   a.bar = bar;
   cudaMemsetAsync(iwork, 0, 30 * sizeof(int), st);
   cudaMemsetAsync(bar.count, 0, sizeof(unsigned), st);
-  static int grid = 0;
-  if (grid == 0) grid = jacobi_max_grid();
+  static const int grid = jacobi_max_grid();  // thread-safe one-time initialisation
   int g = grid;
+  if (coop_grid_cap() > 0 && g > coop_grid_cap()) g = coop_grid_cap();
   const int64_t need = (int64_t(m + 1) * (m + 1) / 4 + 255) / 256;
   if (g > need) g = (int)need;
   if (g < 1) g = 1;

@@ -25,6 +25,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -36,7 +38,15 @@
 
 namespace mmd {
 
-int64_t g_kernel_launches = 0;
+
+// MMD_DEBUG=1 in the environment prints a per-level trace to stderr.
+static bool debug_on() {
+  static const bool v = [] {
+    const char* e = getenv("MMD_DEBUG");
+    return e && e[0] && e[0] != '0';
+  }();
+  return v;
+}
 
 struct Workspace {
   std::map<std::string, std::pair<void*, size_t>> bufs;
@@ -190,10 +200,12 @@ struct Ctx {
   // ---- the persistent solver
   // mode 0: CG on A_k; 1: flexible PCG with M_k; 2: CG on P A_k P (patches of level k+1)
   // B: rhs (n x m, ld n); X: initial guess (x0 = 1) / solution.  In the mixed
-  // mode the FP32 solver runs inside FP64 iterative refinement.
+  // modes the FP32 solver runs inside FP64 iterative refinement (MMD_MIXED:
+  // levels k >= 1, whose conditioning the decomposition bounds; MMD_MIXED_ALL:
+  // level 0 too).
   void solve(int k, int mode, const double* B, double* X, int m, int x0, double tol, int maxit,
              std::vector<int64_t>* iters, int64_t* inner_total, int* notconv) {
-    if (o.precision == MMD_MIXED) {
+    if ((o.precision == MMD_MIXED && k >= 1) || o.precision == MMD_MIXED_ALL) {
       solve_mixed(k, mode, B, X, m, x0, tol, maxit, iters, inner_total, notconv);
       return;
     }
@@ -205,7 +217,21 @@ struct Ctx {
   void solve_mixed(int k, int mode, const double* B, double* X, int m, int x0, double tol, int maxit,
                    std::vector<int64_t>* iters, int64_t* inner_total, int* notconv) {
     if (mode == 0) {  // level-0 CG: FP32 recurrences with FP64 reliable updates, one launch
-      solve_raw(k, 0, true, nullptr, nullptr, m, x0, tol, maxit, iters, inner_total, notconv, B, X);
+      std::vector<int64_t> its;
+      std::vector<int> cv;
+      solve_raw(k, 0, true, nullptr, nullptr, m, x0, tol, maxit, &its, inner_total, nullptr, B, X, &cv);
+      // columns FP32 could not finish continue in FP64 CG from their current X
+      const int64_t n = h->dl[k].n;
+      for (int c = 0; c < m; ++c) {
+        if (!cv[c]) {
+          std::vector<int64_t> its64;
+          solve_raw(k, 0, false, B + size_t(c) * n, X + size_t(c) * n, 1, 1, tol, maxit, &its64, inner_total,
+                    notconv);
+          its[c] += its64[0];
+          S.fp64_finishes += 1;
+        }
+        if (iters) iters->push_back(its[c]);
+      }
       return;
     }
     const DLevel& L = h->dl[k];
@@ -263,11 +289,14 @@ struct Ctx {
 
   void solve_raw(int k, int mode, bool fp32, const void* B, void* X, int m, int x0, double tol, int maxit,
                  std::vector<int64_t>* iters, int64_t* inner_total, int* notconv, const double* B64 = nullptr,
-                 double* X64 = nullptr) {
+                 double* X64 = nullptr, std::vector<int>* conv_out = nullptr) {
     const DLevel& L = h->dl[k];
     const int64_t n = L.n;
     const int MT = (m > 1) ? 8 : 1;
-    const int grid = solver_max_grid(MT, ws->nsm);
+    // one block per 1024 rows (at least 16, at most one per SM): small levels
+    // leave SMs free for other solves running concurrently on other streams
+    int grid = std::min(solver_max_grid(MT, ws->nsm), std::max(16, (int)((n + 1023) / 1024)));
+    if (coop_grid_cap() > 0) grid = std::min(grid, coop_grid_cap());
     if (grid < 1) {
       set_error("solver kernel cannot be made resident");
       throw CudaFail{MMD_ECUDA};
@@ -341,6 +370,7 @@ struct Ctx {
       int64_t itmax = 0, itsum = 0;
       for (int c = 0; c < mc; ++c) {
         if (iters) iters->push_back(its[c]);
+        if (conv_out) conv_out->push_back(cv[c]);
         if (!cv[c] && notconv) ++*notconv;
         itmax = std::max(itmax, its[c]);
         itsum += its[c];
@@ -597,6 +627,13 @@ ExtendOut extend(Ctx& c, int k, double* BAS, int m0, int cap, const std::vector<
     for (int it = 0; it < c.o.max_restarts; ++it) {
       std::vector<double> th, res;
       lz.ritz(th, res);
+      if (debug_on()) {
+        double worst = 0;
+        for (size_t i = 0; i < th.size(); ++i)
+          worst = std::max(worst, res[i] / (relative ? tol_rel * std::fabs(th[i]) : eps_abs));
+        fprintf(stderr, "[mmd] level %d converge j=%d worst res/limit=%.3e theta=[%.6e..%.6e]\n", k, lz.j, worst,
+                th.front(), th.back());
+      }
       if (res_ok(th, res)) return;
       const int pe = std::min(std::max(pp, lz.j), room - lz.j);
       if (pe <= 0) return;
@@ -633,6 +670,7 @@ ExtendOut extend(Ctx& c, int k, double* BAS, int m0, int cap, const std::vector<
   CK(cudaMemcpyAsync(lz.V(), T, sizeof(double) * size_t(n) * jn, cudaMemcpyDeviceToDevice, c.st));
   c.S.kernel_launches += 1;
   out.m = m0 + jn;
+  if (debug_on()) fprintf(stderr, "[mmd] level %d extend m0=%d new=%d steps=%d\n", k, m0, jn, lz.steps);
   for (int i = jn - 1; i >= 0; --i) out.D.push_back(th[i]);
   return out;
 }
@@ -773,6 +811,7 @@ int refine(Ctx& c, int k, double* Q0, std::vector<double>& D, double tol_rel, do
   }
   CK(cudaMemcpyAsync(Qout, Q, sizeof(double) * size_t(n) * mh, cudaMemcpyDeviceToDevice, c.st));
   D.resize(mh);
+  if (debug_on()) fprintf(stderr, "[mmd] level %d refine m=%d mh=%d done=%d\n", k, m, mh, (int)done);
   return mh;
 }
 
@@ -870,6 +909,43 @@ int level_op(mmd_handle* h, int k, const double* x, double* y, double tol, int m
   return MMD_OK;
 }
 
+// Y = OP(X) for m columns: the multi-right-hand-side solve of the refinement
+// (Algorithm 5) on caller vectors, in tiles of 8 columns per launch.
+int level_op_block(mmd_handle* h, int k, int m, const double* x, double* y, double tol, int max_iter,
+                   int64_t* iters, int precision, cudaStream_t st) {
+  try {
+    mmd_eig_opts o;
+    mmd_default_eig_opts(&o);
+    o.max_cg_iter = max_iter;
+    o.precision = precision;
+    Ctx c(h, st, o);
+    CK(cudaMemsetAsync(c.ws->status, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(c.ws->bar, 0, 2 * sizeof(unsigned), st));
+    const DLevel& L = h->dl[k];
+    double* a = buf<double>(c.ws, "lb_a", size_t(L.n) * m);
+    double* b = buf<double>(c.ws, "lb_b", size_t(L.n) * m);
+    double* z = buf<double>(c.ws, "lb_z", size_t(L.n) * m);
+    k_gather(x, L.n, L.d_perm, L.n, m, a, L.n, st);
+    c.spmv(k, 1, a, b, m);
+    std::vector<int64_t> its;
+    int64_t inner = 0;
+    int nc = 0;
+    c.solve(k, k == 0 ? 0 : 1, b, z, m, 0, tol, max_iter, &its, &inner, &nc);
+    k_scatter(z, L.n, L.d_perm, L.n, m, y, L.n, st);
+    c.sync();
+    CK(cudaGetLastError());
+    if (iters)
+      for (int i = 0; i < m; ++i) iters[i] = its[i];
+    if (nc) {
+      set_error("mmd_level_op_block: PCG reached max_iter");
+      return MMD_ENOCONV;
+    }
+  } catch (const CudaFail& f) {
+    return f.code;
+  }
+  return MMD_OK;
+}
+
 int level_bsolve(mmd_handle* h, int k, const double* q, double* x, double tol, int max_iter, int64_t* iters,
                  cudaStream_t st) {
   try {
@@ -901,6 +977,16 @@ int level_bsolve(mmd_handle* h, int k, const double* q, double* x, double tol, i
     return f.code;
   }
   return MMD_OK;
+}
+
+// Wall time of level k's work (coarsest solve, or refinement + extension),
+// Section 7's per-level computation time.
+static void S_level_mark(Ctx& c, int k, std::chrono::steady_clock::time_point t0) {
+  const double now = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  double prev = 0;
+  for (int j = 0; j < 16; ++j) prev += c.S.t_level_ms[j];
+  c.S.t_level_ms[k] = now - prev;
+  if (debug_on()) fprintf(stderr, "[mmd] level %d time %.1f ms\n", k, now - prev);
 }
 
 int run_eig(mmd_handle* h, int N, double tol, const mmd_eig_opts& o, double* lambda, double* Vout, int outdev,
@@ -951,6 +1037,8 @@ int run_eig(mmd_handle* h, int N, double tol, const mmd_eig_opts& o, double* lam
       Vh = buf<double>(c.ws, "V_cur", size_t(nK) * std::max(m, 1));
       if (m) CK(cudaMemcpyAsync(Vh, Z, sizeof(double) * size_t(nK) * m, cudaMemcpyDeviceToDevice, st));
       uint64_t stream = 1000;
+      c.sync();
+      if (K < 16) S_level_mark(c, K, t0);
       for (int k = K - 1; k >= 0; --k) {
         const DLevel& L = h->dl[k];
         const int64_t n = L.n;
@@ -987,6 +1075,8 @@ int run_eig(mmd_handle* h, int N, double tol, const mmd_eig_opts& o, double* lam
         m = ex.m;
         D = ex.D;
         Vh = BAS;
+        c.sync();
+        if (k < 16) S_level_mark(c, k, t0);
       }
     }
     // ---- outputs: N largest mu -> ascending lambda, natural order, normalised
@@ -1031,6 +1121,13 @@ int run_eig(mmd_handle* h, int N, double tol, const mmd_eig_opts& o, double* lam
     const cudaMemcpyKind kv = outdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const cudaMemcpyKind kl = outdev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
     if (nout) CK(cudaMemcpyAsync(Vout, Vn, sizeof(double) * size_t(n0) * nout, kv, st));
+    // keep the result for eig_grad
+    if (nout) {
+      double* lv = buf<double>(c.ws, "last_V", size_t(n0) * nout);
+      CK(cudaMemcpyAsync(lv, Vn, sizeof(double) * size_t(n0) * nout, cudaMemcpyDeviceToDevice, st));
+    }
+    h->last_lam.assign(lam.begin(), lam.begin() + nout);
+    h->last_N = nout;
     if (kl == cudaMemcpyHostToHost)
       std::memcpy(lambda, lam.data(), sizeof(double) * N);
     else
@@ -1050,6 +1147,130 @@ int run_eig(mmd_handle* h, int N, double tol, const mmd_eig_opts& o, double* lam
     cp->S.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = cp->S;
     delete cp;
+  }
+  return rc;
+}
+
+// ------------------------------------------------------------ adjoint
+// dL/dval for every stored entry of the input CSR from the last eig_leftmost
+// result (lambda_i, v_i), i < N, and the loss gradients gl = dL/dlambda,
+// Gv = dL/dV (may be NULL):
+//   U = V diag(gl) + Y,  y_i = -(A - lambda_i I)^+ g_i  (in-block terms plus
+//   a CG solve of (A - lambda_i I) z = -(I - V V^T) g_i on range(I - V V^T)),
+//   G_e = sum_i U(r_e, i) V(c_e, i).
+int run_grad(mmd_handle* h, const double* gl_in, const double* Gv_in, int in_dev, double* out, int out_dev,
+             const mmd_eig_opts& o) {
+  cudaStream_t st = (cudaStream_t)o.stream;
+  int rc = MMD_OK;
+  try {
+    Ctx c(h, st, o);
+    const int N = h->last_N;
+    const int64_t n = h->A0.nrows, nnz = h->A0.nnz();
+    if (N < 1) {
+      set_error("eig_grad: no eig_leftmost result on this handle");
+      return MMD_EINVAL;
+    }
+    double* V = buf<double>(c.ws, "last_V", size_t(n) * N);
+    double* U = buf<double>(c.ws, "gr_U", size_t(n) * N);
+    double* Gv = buf<double>(c.ws, "gr_Gv", size_t(n) * N);
+    double* gld = buf<double>(c.ws, "gr_gl", N);
+    const cudaMemcpyKind ki = in_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(gld, gl_in, sizeof(double) * N, ki, st));
+    CK(cudaMemcpyAsync(U, V, sizeof(double) * size_t(n) * N, cudaMemcpyDeviceToDevice, st));
+    k_scale_cols(U, n, n, N, gld, st);
+    c.after_launch();
+    if (Gv_in) {
+      CK(cudaMemcpyAsync(Gv, Gv_in, sizeof(double) * size_t(n) * N, ki, st));
+      std::vector<double> gn = c.dots_host(Gv, Gv, n, N);
+      // C = V^T Gv (N x N) -> in-block coefficients D_ji = C_ji / (lambda_i - lambda_j)
+      double* Cd = buf<double>(c.ws, "gr_C", size_t(N) * N);
+      const size_t gsl = std::max<size_t>(size_t(8) << 20, size_t(N) * N * 4);
+      double* gs = buf<double>(c.ws, "gemm_scratch", gsl);
+      k_gemm_tn(N, N, n, 1.0, V, n, Gv, n, 0.0, Cd, N, gs, gsl, st);
+      c.after_launch();
+      std::vector<double> C(size_t(N) * N), D(size_t(N) * N, 0.0);
+      CK(cudaMemcpyAsync(C.data(), Cd, sizeof(double) * N * N, cudaMemcpyDeviceToHost, st));
+      c.sync();
+      const std::vector<double>& lam = h->last_lam;
+      for (int i = 0; i < N; ++i) {
+        if (!(gn[i] > 0)) continue;
+        for (int j = 0; j < N; ++j)
+          if (j != i && std::fabs(lam[i] - lam[j]) > 1e-14 * std::max(std::fabs(lam[i]), 1.0))
+            D[j + size_t(i) * N] = C[j + size_t(i) * N] / (lam[i] - lam[j]);
+      }
+      CK(cudaMemcpyAsync(Cd, D.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice, st));
+      k_gemm_nn(n, N, N, 1.0, V, n, Cd, N, 1.0, U, n, st);  // U += V D
+      c.after_launch();
+      // complement: (A - lambda_i I) z = -(I - V V^T) g_i, CG on range(I - V V^T)
+      // (natural order: the level-0 matrix is applied through gather/scatter)
+      const DLevel& L0 = h->dl[0];
+      double* z = buf<double>(c.ws, "gr_z", n);
+      double* r = buf<double>(c.ws, "gr_r", n);
+      double* p = buf<double>(c.ws, "gr_p", n);
+      double* q = buf<double>(c.ws, "gr_q", n);
+      double* t1 = buf<double>(c.ws, "gr_t1", n);
+      double* t2 = buf<double>(c.ws, "gr_t2", n);
+      double* hv = buf<double>(c.ws, "gr_h", N);
+      double* sc = buf<double>(c.ws, "lz_sc", size_t((n + 2047) / 2048) * N + 64);
+      auto project = [&](double* x) {
+        k_gemv_t(V, n, n, N, x, hv, sc, st);
+        k_gemv_n(V, n, n, N, hv, -1.0, x, st);
+        c.S.kernel_launches += 3;
+      };
+      auto apply = [&](const double* x, double shift, double* y) {  // y = P (A - shift I) x
+        k_gather(x, n, L0.d_perm, n, 1, t1, n, st);
+        k_spmv(sell_of(L0.A), t1, n, t2, n, 1, st);
+        k_scatter(t2, n, L0.d_perm, n, 1, y, n, st);
+        k_axpy(y, x, n, -shift, st);
+        c.S.kernel_launches += 4;
+        project(y);
+      };
+      for (int i = 0; i < N; ++i) {
+        if (!(gn[i] > 0)) continue;
+        k_copy(r, Gv + size_t(i) * n, n, st);
+        k_scal(r, n, -1.0, st);
+        project(r);
+        k_fill(z, n, 0.0, st);
+        k_copy(p, r, n, st);
+        c.S.kernel_launches += 4;
+        double rr = c.dots_host(r, r, n, 1)[0];
+        const double bn = std::sqrt(rr);
+        for (int it = 0; it < o.max_cg_iter && std::sqrt(rr) > 1e-12 * bn && bn > 0; ++it) {
+          apply(p, lam[i], q);
+          const double pq = c.dots_host(p, q, n, 1)[0];
+          if (!(pq > 0)) {
+            set_error("eig_grad: the shifted complement operator is not positive definite "
+                      "(lambda_i >= lambda_{N+1}?)");
+            throw CudaFail{MMD_ENOTSPD};
+          }
+          const double al = rr / pq;
+          k_axpy(z, p, n, al, st);
+          k_axpy(r, q, n, -al, st);
+          const double rn = c.dots_host(r, r, n, 1)[0];
+          k_scal(p, n, rn / rr, st);
+          k_axpy(p, r, n, 1.0, st);
+          c.S.kernel_launches += 4;
+          rr = rn;
+        }
+        project(z);
+        k_axpy(U + size_t(i) * n, z, n, 1.0, st);
+        c.after_launch();
+      }
+    }
+    // G_e = sum_i U(r_e, i) V(c_e, i) over the input pattern
+    if (!h->d_in_rowptr) {
+      CK(cudaMalloc(&h->d_in_rowptr, sizeof(int32_t) * (n + 1)));
+      CK(cudaMalloc(&h->d_in_col, sizeof(int32_t) * nnz));
+      CK(cudaMemcpy(h->d_in_rowptr, h->A0.rowptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(h->d_in_col, h->A0.col.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
+    }
+    double* G = out_dev ? out : buf<double>(c.ws, "gr_G", nnz);
+    k_sddmm(h->d_in_rowptr, h->d_in_col, n, U, V, n, N, G, st);
+    c.after_launch();
+    if (!out_dev) CK(cudaMemcpyAsync(out, G, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st));
+    c.sync();
+  } catch (const CudaFail& f) {
+    rc = f.code;
   }
   return rc;
 }

@@ -10,13 +10,16 @@ namespace mmd {
 int level_spmv(mmd_handle* h, int k, int which, const double* x, double* y, cudaStream_t st);
 int level_op(mmd_handle* h, int k, const double* x, double* y, double tol, int max_iter, int64_t* iters,
              cudaStream_t st);
+int level_op_block(mmd_handle* h, int k, int m, const double* x, double* y, double tol, int max_iter,
+                   int64_t* iters, int precision, cudaStream_t st);
 int level_bsolve(mmd_handle* h, int k, const double* q, double* x, double tol, int max_iter, int64_t* iters,
                  cudaStream_t st);
 int run_eig(mmd_handle* h, int N, double tol, const mmd_eig_opts& o, double* lambda, double* V, int outdev,
             mmd_eig_stats* stats);
+int run_grad(mmd_handle* h, const double* gl, const double* Gv, int in_dev, double* out, int out_dev,
+             const mmd_eig_opts& o);
 void free_workspace(mmd_handle* h);
 
-extern int64_t g_kernel_launches;
 void set_tri_scratch(double* bounds, double* e2, int* cstart, int* ncl, double* work, int* iwork);
 
 }  // namespace mmd

@@ -49,7 +49,7 @@ struct SolverArgs {
   GridBarrier bar;
 };
 
-int solver_threads();
+int solver_threads(int mt);
 int solver_max_grid(int mt, int num_sms);
 cudaError_t launch_solver(const SolverArgs& a, int mt, int grid, cudaStream_t st);
 
@@ -84,6 +84,9 @@ void k_scatter(const double* x, int64_t ldx, const int32_t* perm, int64_t n, int
 // project each column onto range(P): x -= phi (phi^T x) per segment
 void k_project(double* x, int64_t ld, int m, const int32_t* seg_ptr, const double* phi, int64_t nseg,
                cudaStream_t st);
+// G[e] = sum_i U(r_e, i) V(c_e, i) over a CSR pattern (U, V: n x N, ld)
+void k_sddmm(const int32_t* rp, const int32_t* ci, int64_t n, const double* U, const double* V, int64_t ld, int N,
+             double* G, cudaStream_t st);
 // r = b - y (FP64); f = (float) d; x += (double) f  (n x m, ld n)
 void k_sub(double* r, const double* b, const double* y, int64_t n, cudaStream_t st);
 void k_to_f32(float* f, const double* d, int64_t n, cudaStream_t st);
@@ -118,6 +121,12 @@ int k_syev(double* A, int lda, int n, double* w, double* Z, int ldz, double* wor
 // parallel two-sided Jacobi (cooperative): S (m x m, ld m) -> diagonal (eigenvalues, unsorted),
 // V (m x m) eigenvectors; work >= m + 4 doubles, iwork >= 30 ints
 cudaError_t k_syev_jacobi(double* S, int m, double* V, double* work, int* iwork, GridBarrier bar, cudaStream_t st);
+
+// Upper bound on the blocks of the calling host thread's cooperative launches
+// (0 = none).  Concurrent solves on several streams split the SMs so that
+// every cooperative grid stays resident next to the others.
+void set_coop_grid_cap(int blocks);
+int coop_grid_cap();
 // B(:, c) = A(:, perm[c])
 void k_permute_cols(const double* A, int lda, int64_t nrows, const int* perm, int ncols, double* B, int ldb,
                     cudaStream_t st);

@@ -79,6 +79,12 @@ struct mmd_handle {
   std::vector<mmd::DLevel> dl;       // k = 0..K
   mmd::Workspace* ws = nullptr;
   double normA_inf = 0;
+  // last eig_leftmost result (for eig_grad): eigenvalues ascending (host),
+  // eigenvectors in natural order in the workspace buffer "last_V"
+  std::vector<double> last_lam;
+  int last_N = 0;
+  int32_t* d_in_rowptr = nullptr;  // input CSR pattern (natural order), uploaded by eig_grad
+  int32_t* d_in_col = nullptr;
 };
 
 namespace mmd {

@@ -3,17 +3,18 @@
 // by an inner CG to 0.1 eps) and of the two solves of the Eigenpair
 // Refinement (Algorithm 5: CG on B^(l) = U^T A U and the warm-started PCG).
 //
-// One cooperative launch (one 1024-thread block per SM) runs a whole solve for
-// m <= MT right-hand sides (column-major, leading dimension ld).  Scalars never
-// leave the device: each block writes its partial sums, a bounded grid barrier
+// One cooperative launch (one block per SM: 1024 threads, 512 for eight
+// columns) runs a whole solve for m <= MT right-hand sides (column-major,
+// leading dimension ld).  Scalars never leave the device: each block writes its partial sums, a bounded grid barrier
 // follows, and every block then reduces the same partials in the same order,
 // so all blocks take identical decisions.
 //
 // GB300 retires about one FP64 warp-instruction per 16 SM cycles, so the
 // kernel is organised to issue as few FP64 instructions as the arithmetic
 // needs: the matrices are in SELL-32 (one row per lane, one FMA per stored
-// entry, no shuffle reductions inside a row), and a block reduction is one
-// pass of warp 0 over the threads' partials in shared memory.
+// entry, no shuffle reductions inside a row), and a block reduction adds the
+// threads' partials from shared memory with all lanes busy, the columns (or
+// quarters of one column) spread over the SM's sub-partitions.
 //
 // Precision: T = double (every step FP64) or T = float (matrix values,
 // vectors and per-thread sums in FP32; block sums and scalars in FP64).  The
@@ -33,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "dev_common.cuh"
 #include "kernels.h"
@@ -41,55 +43,74 @@ namespace mmd {
 
 namespace {
 
-constexpr int kThreads = 1024;
+// Threads per block (one block per SM): 1024 for one right-hand side; 512
+// for the eight-column tiles, whose eight accumulators per row need the 128
+// registers a thread gets at 512 threads per SM.
+template <int MT>
+__host__ __device__ constexpr int threads_for() {
+  return MT == 1 ? 1024 : 512;
+}
+constexpr int kMaxThreads = 1024;
 
 template <int MT>
 struct Sh {
-  double part[kThreads + 1];
+  double quart[MT * 4];  // block reduction: per-warp sums, up to 4 warps per column
   double bn[MT], rz[MT], rr[MT], alpha[MT], val[MT], val2[MT];
   double irr[MT], irn0[MT], ia[MT];
   int act[MT], iact[MT];
+  int due[MT], stag[MT];  // reliable updates: replacement due / no progress since the last one
+  int ok[MT];             // reliable updates: stopped with the true residual below tol
   long long it[MT], iit[MT];
 };
 
-// Block sum: every thread stores its partial; warp 0 adds 32 per lane and
-// shuffles (37 FP64 warp-instructions per block instead of a shuffle tree in
-// all 32 warps).  Result in part[kThreads].
-__device__ __forceinline__ void block_reduce_to(double v, double* part) {
-  part[threadIdx.x] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = 0.0;
-#pragma unroll 8
-    for (int i = threadIdx.x; i < kThreads; i += 32) t += part[i];
-    t = warp_sum(t);
-    if (threadIdx.x == 0) part[kThreads] = t;
-  }
-  __syncthreads();
-}
+// Per-thread partial sums of the block, [MT][threads] doubles of dynamic
+// shared memory (8 KB for one column, 32 KB for eight).
+extern __shared__ double g_part[];
 
-// partial sums red[slot][c][block] -> dst[c] (shared) in every block; one warp
+// partial sums red[slot][c][block] -> dst[c] (shared) in every block; warp c
+// sums column c, so the columns are reduced on different SM sub-partitions
 template <int MT>
 __device__ void reduce_slot(const double* red, int slot, int m, double* dst) {
-  const int G = gridDim.x;
-  if (threadIdx.x < 32) {
-    for (int c = 0; c < m; ++c) {
-      const double* p = red + (size_t(slot) * MT + c) * G;
-      double t = 0.0;
-      for (int b = threadIdx.x; b < G; b += 32) t += p[b];
-      t = warp_sum(t);
-      if (threadIdx.x == 0) dst[c] = t;
-    }
+  const int G = gridDim.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < m) {
+    const double* p = red + (size_t(slot) * MT + w) * G;
+    double t = 0.0;
+    for (int b = lane; b < G; b += 32) t += p[b];
+    t = warp_sum(t);
+    if (lane == 0) dst[w] = t;
   }
   __syncthreads();
 }
 
+// Block sums of acc[c], c < m, written to red[slot][c][blockIdx].  Every
+// thread stores its partials; then wpc warps per column (4 for one or two
+// columns, 2 for up to four, else 1) each add a contiguous share with all 32
+// lanes busy and finish with one shuffle tree.  Consecutive warps sit on
+// different SM sub-partitions, so the FP64 adds of the columns proceed in
+// parallel instead of queueing behind one warp.  Fixed order: deterministic.
 template <int MT, typename T>
 __device__ void write_partials(double* red, int slot, int m, const T* acc, Sh<MT>& s) {
-  for (int c = 0; c < m; ++c) {
-    block_reduce_to((double)acc[c], s.part);
-    if (threadIdx.x == 0) red[(size_t(slot) * MT + c) * gridDim.x + blockIdx.x] = s.part[kThreads];
-    __syncthreads();
+  constexpr int NT = threads_for<MT>();
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+#pragma unroll
+  for (int c = 0; c < MT; ++c)
+    if (c < m) g_part[c * NT + tid] = (double)acc[c];
+  __syncthreads();
+  const int wpc = (m <= 2) ? 4 : (m <= 4 ? 2 : 1);
+  const int span = NT / wpc;
+  if (w < m * wpc) {
+    const int c = w / wpc, q = w - c * wpc;
+    const double* p = g_part + c * NT + q * span;
+    double t = 0.0;
+    for (int i = lane; i < span; i += 32) t += p[i];
+    t = warp_sum(t);
+    if (lane == 0) s.quart[c * 4 + q] = t;
+  }
+  __syncthreads();
+  if (tid < m) {
+    double t = s.quart[tid * 4];
+    for (int q = 1; q < wpc; ++q) t += s.quart[tid * 4 + q];
+    red[(size_t(slot) * MT + tid) * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -168,7 +189,7 @@ __device__ bool inner_cg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nt
   }
   __syncthreads();
   for (int64_t i = tid; i < n; i += nthr)
-    for (int c = 0; c < m; ++c)
+    _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
       if (s.act[c]) {
         const T rv = r[i + c * ld];
         z[i + c * ld] = T(0);
@@ -178,7 +199,7 @@ __device__ bool inner_cg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nt
   if (!grid_sync(a.bar)) return false;
   for (int j = 1; j <= a.imaxit; ++j) {
     int any = 0;
-    for (int c = 0; c < m; ++c) any |= s.iact[c];
+    _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) any |= s.iact[c];
     if (!any) break;
 #pragma unroll
     for (int c = 0; c < MT; ++c) acc[c] = T(0);
@@ -191,7 +212,7 @@ __device__ bool inner_cg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nt
 #pragma unroll
     for (int c = 0; c < MT; ++c) acc[c] = T(0);
     for (int64_t i = tid; i < n; i += nthr)
-      for (int c = 0; c < m; ++c)
+      _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
         if (s.iact[c]) {
           const int64_t o = i + c * ld;
           const T al = (T)s.ia[c];
@@ -215,7 +236,7 @@ __device__ bool inner_cg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nt
     }
     __syncthreads();
     for (int64_t i = tid; i < n; i += nthr)
-      for (int c = 0; c < m; ++c)
+      _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
         if (s.iact[c]) {
           const int64_t o = i + c * ld;
           ip[o] = fma((T)s.ia[c], ip[o], ir[o]);
@@ -224,7 +245,7 @@ __device__ bool inner_cg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nt
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     long long t = 0;
-    for (int c = 0; c < m; ++c) t += s.iit[c];
+    _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) t += s.iit[c];
     *a.in_out += t;
   }
   return true;
@@ -246,7 +267,7 @@ __device__ bool cgcg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr) 
   T acc[MT];
   for (int it = 1; it <= a.maxit; ++it) {
     int any = 0;
-    for (int c = 0; c < m; ++c) any |= s.act[c];
+    _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) any |= s.act[c];
     if (!any) break;
     // w = A r, delta = r^T w
 #pragma unroll
@@ -279,7 +300,7 @@ __device__ bool cgcg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr) 
     for (int c = 0; c < MT; ++c) acc[c] = T(0);
     const bool first = (it == 1);
     for (int64_t i = tid; i < n; i += nthr)
-      for (int c = 0; c < m; ++c)
+      _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
         if (s.act[c]) {
           const int64_t o = i + c * ld;
           const T be = (T)s.val2[c], al = (T)s.alpha[c];
@@ -311,8 +332,8 @@ __device__ bool cgcg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr) 
 
 // FP64 residual of the reliable update: rr32 = (float)(b64 - A x64), partial
 // sums of its square; FP64 SELL SpMV (matrix values in FP64).
-template <int MT>
-__device__ void reliable_residual(const SolverArgs& a, const int* mask, float* r32, double* acc) {
+template <int MT, typename T>
+__device__ void reliable_residual(const SolverArgs& a, const int* mask, T* r32, double* acc) {
   const Sell& A = a.A;
   const int m = a.m;
   const int64_t ld = a.ld;
@@ -337,30 +358,34 @@ __device__ void reliable_residual(const SolverArgs& a, const int* mask, float* r
       for (int c = 0; c < MT; ++c)
         if (c < m && mask[c]) {
           const double rv = a.b64[row + c * ld] - ax[c];
-          r32[row + c * ld] = (float)rv;
+          r32[row + c * ld] = (T)rv;
           acc[c] = fma(rv, rv, acc[c]);
         }
     }
   }
 }
 
-// Mode 0, FP32 with FP64 reliable updates (residual replacement): the CG
-// recurrences run in FP32, x accumulates in FP64, and whenever the FP32
-// residual has dropped by 100x since the last replacement -- and before
-// convergence is accepted -- r is replaced by the FP64 residual b - A x.
-// The Krylov recurrence is kept (no restart), so the iteration count stays
-// close to the FP64 one while the SpMV and vector traffic is FP32.
-template <int MT>
-__device__ bool cgcg_rel(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr) {
-  float* const r = (float*)a.r;
-  float* const p = (float*)a.p;
-  float* const w = (float*)a.z;
-  float* const sv = (float*)a.q;
+// Mode 0 with residual replacement (reliable updates; van der Vorst and Ye
+// 2000, as used for mixed-precision CG): Hestenes-Stiefel CG whose
+// recurrences run in T (FP32 in the mixed mode) while x accumulates in FP64.
+// Whenever the recurrence residual has dropped 100x since the last
+// replacement -- and before convergence is accepted -- r is replaced by the
+// FP64 residual b - A x.  The Krylov recurrence is kept (no restart);
+// alpha = r^T r / p^T A p is computed directly, so a replacement needs no
+// further correction.  A column stops unconverged (conv = 0) when its true
+// residual stalls across a replacement or p^T A p <= 0 in FP32 -- FP32
+// cannot resolve directions whose Rayleigh quotient is below about
+// u_32 ||A||, as for the 1e-6-shifted Laplacians -- and the caller finishes
+// it with FP64 CG from the current x.
+template <int MT, typename T>
+__device__ bool cg_rel(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr) {
+  T* const r = (T*)a.r;
+  T* const p = (T*)a.p;
+  T* const q = (T*)a.q;
   const int m = a.m;
   const int64_t n = a.n, ld = a.ld;
-  float acc[MT];
+  T acc[MT];
   double dacc[MT];
-  // initial residual in FP64 (x64 = x0 or 0)
   int all1[MT];
 #pragma unroll
   for (int c = 0; c < MT; ++c) {
@@ -369,14 +394,14 @@ __device__ bool cgcg_rel(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nt
   }
   if (!a.x0)
     for (int64_t i = tid; i < n; i += nthr)
-      for (int c = 0; c < m; ++c) a.x64[i + c * ld] = 0.0;
+      _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) a.x64[i + c * ld] = 0.0;
   if (!grid_sync(a.bar)) return false;
-  reliable_residual<MT>(a, all1, r, dacc);
+  reliable_residual<MT, T>(a, all1, r, dacc);
   write_partials<MT, double>(a.red, 1, m, dacc, s);
 #pragma unroll
   for (int c = 0; c < MT; ++c) dacc[c] = 0.0;
   for (int64_t i = tid; i < n; i += nthr)
-    for (int c = 0; c < m; ++c) dacc[c] = fma(a.b64[i + c * ld], a.b64[i + c * ld], dacc[c]);
+    _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) dacc[c] = fma(a.b64[i + c * ld], a.b64[i + c * ld], dacc[c]);
   write_partials<MT, double>(a.red, 0, m, dacc, s);
   if (!grid_sync(a.bar)) return false;
   reduce_slot<MT>(a.red, 0, m, s.bn);
@@ -385,99 +410,119 @@ __device__ bool cgcg_rel(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nt
     const int c = threadIdx.x;
     s.bn[c] = sqrt(s.bn[c]);
     s.act[c] = (s.bn[c] > 0.0) && !(sqrt(s.rr[c]) <= a.tol * s.bn[c]);
+    s.ok[c] = !s.act[c];
     s.it[c] = 0;
-    s.irn0[c] = sqrt(s.rr[c]);  // norm at the last replacement
+    s.irn0[c] = sqrt(s.rr[c]);  // residual norm at the last replacement
+    s.due[c] = 0;
+    s.stag[c] = 0;
   }
   __syncthreads();
+  for (int64_t i = tid; i < n; i += nthr)
+    _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
+      if (s.act[c]) p[i + c * ld] = r[i + c * ld];
+  if (!grid_sync(a.bar)) return false;
   for (int it = 1; it <= a.maxit; ++it) {
     int any = 0;
-    for (int c = 0; c < m; ++c) any |= s.act[c];
+    _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) any |= s.act[c];
     if (!any) break;
+    // q = A p, p^T q
 #pragma unroll
-    for (int c = 0; c < MT; ++c) acc[c] = 0.0f;
-    spmv_cols<MT, float>(a.A, r, w, ld, m, s.act, r, acc);
-    write_partials<MT, float>(a.red, 0, m, acc, s);
+    for (int c = 0; c < MT; ++c) acc[c] = T(0);
+    spmv_cols<MT, T>(a.A, p, q, ld, m, s.act, p, acc);
+    write_partials<MT, T>(a.red, 0, m, acc, s);
     if (!grid_sync(a.bar)) return false;
     reduce_slot<MT>(a.red, 0, m, s.val);
     if (threadIdx.x < m) {
       const int c = threadIdx.x;
       if (s.act[c]) {
-        const double g = s.rr[c], dl = s.val[c];
-        double be = 0.0, den = dl;
-        if (it > 1) {
-          be = g / s.rz[c];
-          den = dl - be * g / s.alpha[c];
-        }
-        if (!(den > 0.0)) {
+        if (!(s.val[c] > 0.0)) {
+          // FP32 cannot resolve A below u_32 ||A||: the column stops
+          // unconverged (the caller finishes it in FP64); in FP64 it is an error
           s.act[c] = 0;
-          if (blockIdx.x == 0) atomicExch(a.bar.status, (int)DEV_NOTSPD);
+          if (sizeof(T) == 8 && blockIdx.x == 0) atomicExch(a.bar.status, (int)DEV_NOTSPD);
+        } else {
+          s.alpha[c] = s.rr[c] / s.val[c];
         }
-        s.rz[c] = g;
-        s.alpha[c] = g / den;
-        s.val2[c] = be;
       }
     }
     __syncthreads();
+    // x += alpha p (FP64), r -= alpha q, r^T r
 #pragma unroll
-    for (int c = 0; c < MT; ++c) acc[c] = 0.0f;
+    for (int c = 0; c < MT; ++c) acc[c] = T(0);
     for (int64_t i = tid; i < n; i += nthr)
-      for (int c = 0; c < m; ++c)
+      _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
         if (s.act[c]) {
           const int64_t o = i + c * ld;
-          const bool fresh = (it == 1);
-          const float be = (float)s.val2[c], al = (float)s.alpha[c];
-          const float rv0 = r[o];
-          const float pv = fresh ? rv0 : fmaf(be, p[o], rv0);
-          const float svv = fresh ? w[o] : fmaf(be, sv[o], w[o]);
-          p[o] = pv;
-          sv[o] = svv;
-          a.x64[o] = fma(s.alpha[c], (double)pv, a.x64[o]);
-          const float rv = fmaf(-al, svv, rv0);
+          const T al = (T)s.alpha[c];
+          a.x64[o] = fma(s.alpha[c], (double)p[o], a.x64[o]);
+          const T rv = fma(-al, q[o], r[o]);
           r[o] = rv;
-          acc[c] = fmaf(rv, rv, acc[c]);
+          acc[c] = fma(rv, rv, acc[c]);
         }
-    write_partials<MT, float>(a.red, 1, m, acc, s);
+    write_partials<MT, T>(a.red, 1, m, acc, s);
     if (!grid_sync(a.bar)) return false;
-    reduce_slot<MT>(a.red, 1, m, s.val);
-    // replacement needed?  (FP32 residual 100x below the last replaced one, or converged)
+    reduce_slot<MT>(a.red, 1, m, s.val2);
+    // the recurrence drifts from the true residual: replace it after every
+    // two decades of reduction and before accepting convergence
     int need = 0;
-    for (int c = 0; c < m; ++c)
-      if (s.act[c] && (sqrt(s.val[c]) <= 0.01 * s.irn0[c] || sqrt(s.val[c]) <= a.tol * s.bn[c])) need = 1;
-    if (threadIdx.x < m) {
-      const int c = threadIdx.x;
-      if (s.act[c]) {
-        s.it[c] = it;
-        s.rr[c] = s.val[c];
-      }
-    }
-    __syncthreads();
+    _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
+      if (s.act[c] && (sqrt(s.val2[c]) <= 0.01 * s.irn0[c] || sqrt(s.val2[c]) <= a.tol * s.bn[c])) need = 1;
     if (need) {
+      if (threadIdx.x < m) {
+        const int c = threadIdx.x;
+        s.due[c] = s.act[c] && sqrt(s.val2[c]) <= 0.01 * s.irn0[c];
+      }
       int msk[MT];
 #pragma unroll
       for (int c = 0; c < MT; ++c) {
         msk[c] = (c < m) && s.act[c];
         dacc[c] = 0.0;
       }
-      reliable_residual<MT>(a, msk, r, dacc);  // x64 is complete: the barrier above
+      reliable_residual<MT, T>(a, msk, r, dacc);  // x64 complete: barrier above
       write_partials<MT, double>(a.red, 2, m, dacc, s);
       if (!grid_sync(a.bar)) return false;
-      reduce_slot<MT>(a.red, 2, m, s.val2);
+      reduce_slot<MT>(a.red, 2, m, s.val2);  // true residuals replace the recurrence ones
       if (threadIdx.x < m) {
         const int c = threadIdx.x;
         if (s.act[c]) {
-          s.rr[c] = s.val2[c];
-          s.irn0[c] = sqrt(s.val2[c]);
-          if (sqrt(s.val2[c]) <= a.tol * s.bn[c]) s.act[c] = 0;
+          // two decades of recurrence reduction that left the true residual
+          // above half its last value: stalled
+          const double tn = sqrt(s.val2[c]);
+          s.stag[c] = s.due[c] && tn > 0.5 * s.irn0[c];
+          s.irn0[c] = tn;
         }
       }
-      __syncthreads();
     }
+    if (threadIdx.x < m) {
+      const int c = threadIdx.x;
+      if (s.act[c]) {
+        s.it[c] = it;
+        const double gn = s.val2[c];
+        s.val[c] = gn / s.rr[c];  // beta
+        s.rr[c] = gn;
+        // convergence is accepted on a replaced (true) residual only
+        if (need && sqrt(gn) <= a.tol * s.bn[c]) {
+          s.act[c] = 0;
+          s.ok[c] = 1;
+        } else if (need && s.stag[c]) {
+          s.act[c] = 0;  // stalled above tol: reported unconverged
+        }
+      }
+    }
+    __syncthreads();
+    for (int64_t i = tid; i < n; i += nthr)
+      _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
+        if (s.act[c]) {
+          const int64_t o = i + c * ld;
+          p[o] = fma((T)s.val[c], p[o], r[o]);
+        }
+    if (!grid_sync(a.bar)) return false;
   }
   return true;
 }
 
 template <int MT, typename T>
-__global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolverArgs a) {
+__global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs a) {
   __shared__ Sh<MT> s;
   grid_sync_init();
   T* const b = (T*)a.b;
@@ -490,15 +535,13 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolverArgs a) {
   const int64_t n = a.n, ld = a.ld;
   const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t nthr = int64_t(gridDim.x) * blockDim.x;
-  if constexpr (sizeof(T) == 4) {
-    if (a.mode == 0 && a.b64) {
-      if (!cgcg_rel<MT>(a, s, tid, nthr)) return;
-      if (blockIdx.x == 0 && threadIdx.x < m) {
-        a.it_out[threadIdx.x] = s.it[threadIdx.x];
-        a.conv[threadIdx.x] = s.act[threadIdx.x] ? 0 : 1;
-      }
-      return;
+  if (a.mode == 0 && a.b64) {
+    if (!cg_rel<MT, T>(a, s, tid, nthr)) return;
+    if (blockIdx.x == 0 && threadIdx.x < m) {
+      a.it_out[threadIdx.x] = s.it[threadIdx.x];
+      a.conv[threadIdx.x] = s.ok[threadIdx.x];
     }
+    return;
   }
   T acc[MT], acc2[MT];
   int all1[MT];
@@ -511,17 +554,42 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolverArgs a) {
   }
 #pragma unroll
   for (int c = 0; c < MT; ++c) acc[c] = acc2[c] = T(0);
-  for (int64_t i = tid; i < n; i += nthr)
-    for (int c = 0; c < m; ++c) {
-      const int64_t o = i + c * ld;
-      const T bv = b[o];
-      T rv = bv;
-      if (a.x0) rv -= q[o];
-      else x[o] = T(0);
-      r[o] = rv;
-      acc[c] = fma(bv, bv, acc[c]);
-      acc2[c] = fma(rv, rv, acc2[c]);
+  if (a.mode == 2) {
+    // r = P (b - A x0) per segment: a right-hand side projected once by the
+    // caller keeps a rounding-level component along phi, as large as its
+    // projected part when b was nearly parallel to phi; CG could not remove it
+    for (int64_t sg = tid; sg < a.nseg; sg += nthr) {
+      const int32_t s0 = a.seg_ptr[sg], s1 = a.seg_ptr[sg + 1];
+      _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) {
+        T t = T(0);
+        for (int32_t i = s0; i < s1; ++i) {
+          const int64_t o = i + c * ld;
+          t = fma((T)a.phi[i], a.x0 ? b[o] - q[o] : b[o], t);
+        }
+        for (int32_t i = s0; i < s1; ++i) {
+          const int64_t o = i + c * ld;
+          const T bv = b[o];
+          const T rv = fma(-(T)a.phi[i], t, a.x0 ? bv - q[o] : bv);
+          if (!a.x0) x[o] = T(0);
+          r[o] = rv;
+          acc[c] = fma(bv, bv, acc[c]);
+          acc2[c] = fma(rv, rv, acc2[c]);
+        }
+      }
     }
+  } else {
+    for (int64_t i = tid; i < n; i += nthr)
+      _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) {
+        const int64_t o = i + c * ld;
+        const T bv = b[o];
+        T rv = bv;
+        if (a.x0) rv -= q[o];
+        else x[o] = T(0);
+        r[o] = rv;
+        acc[c] = fma(bv, bv, acc[c]);
+        acc2[c] = fma(rv, rv, acc2[c]);
+      }
+  }
   write_partials<MT, T>(a.red, 0, m, acc, s);
   write_partials<MT, T>(a.red, 1, m, acc2, s);
   if (!grid_sync(a.bar)) return;
@@ -535,7 +603,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolverArgs a) {
   }
   __syncthreads();
   for (int64_t i = tid; i < n; i += nthr)  // zero right-hand sides give x = 0
-    for (int c = 0; c < m; ++c)
+    _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
       if (s.bn[c] == 0.0) x[i + c * ld] = T(0);
   if (a.mode == 0) {
     if (!cgcg<MT, T>(a, s, tid, nthr)) return;
@@ -552,7 +620,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolverArgs a) {
 #pragma unroll
     for (int c = 0; c < MT; ++c) acc[c] = T(0);
     for (int64_t i = tid; i < n; i += nthr)
-      for (int c = 0; c < m; ++c)
+      _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
         if (s.act[c]) acc[c] = fma(r[i + c * ld], z[i + c * ld], acc[c]);
     write_partials<MT, T>(a.red, 0, m, acc, s);
     if (!grid_sync(a.bar)) return;
@@ -562,13 +630,13 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolverArgs a) {
     __syncthreads();
   }
   for (int64_t i = tid; i < n; i += nthr)
-    for (int c = 0; c < m; ++c)
+    _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
       if (s.act[c]) p[i + c * ld] = zv[i + c * ld];
   if (!grid_sync(a.bar)) return;
 
   for (int it = 1; it <= a.maxit; ++it) {
     int any = 0;
-    for (int c = 0; c < m; ++c) any |= s.act[c];
+    _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) any |= s.act[c];
     if (!any) break;
     // q = A p, p^T q
 #pragma unroll
@@ -596,7 +664,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolverArgs a) {
     if (a.mode == 2) {
       for (int64_t sg = tid; sg < a.nseg; sg += nthr) {
         const int32_t s0 = a.seg_ptr[sg], s1 = a.seg_ptr[sg + 1];
-        for (int c = 0; c < m; ++c) {
+        _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) {
           if (!s.act[c]) continue;
           const T al = (T)s.alpha[c];
           T t = T(0);
@@ -613,7 +681,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolverArgs a) {
       }
     } else {
       for (int64_t i = tid; i < n; i += nthr)
-        for (int c = 0; c < m; ++c)
+        _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
           if (s.act[c]) {
             const int64_t o = i + c * ld;
             const T al = (T)s.alpha[c];
@@ -646,7 +714,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolverArgs a) {
 #pragma unroll
       for (int c = 0; c < MT; ++c) acc[c] = acc2[c] = T(0);
       for (int64_t i = tid; i < n; i += nthr)
-        for (int c = 0; c < m; ++c)
+        _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
           if (s.act[c]) {
             const int64_t o = i + c * ld;
             acc[c] = fma(r[o], z[o], acc[c]);
@@ -676,7 +744,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolverArgs a) {
     }
     __syncthreads();
     for (int64_t i = tid; i < n; i += nthr)
-      for (int c = 0; c < m; ++c)
+      _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
         if (s.act[c]) {
           const int64_t o = i + c * ld;
           p[o] = fma((T)s.alpha[c], p[o], zv[o]);
@@ -690,29 +758,46 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(SolverArgs a) {
   }
 }
 
+template <int MT>
+constexpr size_t dyn_smem() {
+  return sizeof(double) * size_t(MT) * threads_for<MT>();
+}
+
+// the 64 KB of the eight-column instance exceed the default 48 KB window
+template <int MT, typename T>
+void allow_smem() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(solve_kernel<MT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem<MT>());
+  });
+}
+
 template <int MT, typename T>
 int max_blocks_for() {
+  allow_smem<MT, T>();
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<MT, T>, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<MT, T>, threads_for<MT>(), dyn_smem<MT>());
   return nb;
 }
 
 template <int MT, typename T>
 cudaError_t launch_tpl(const SolverArgs& a, int grid, cudaStream_t st) {
+  allow_smem<MT, T>();
   void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel((const void*)solve_kernel<MT, T>, dim3(grid), dim3(kThreads), args, 0, st);
+  return cudaLaunchCooperativeKernel((const void*)solve_kernel<MT, T>, dim3(grid), dim3(threads_for<MT>()), args,
+                                     dyn_smem<MT>(), st);
 }
 
 }  // namespace
 
-int solver_threads() { return kThreads; }
+int solver_threads(int mt) { return mt == 1 ? threads_for<1>() : threads_for<8>(); }
 
 // One block per SM (the reductions read one partial per block, <= 1024).
 int solver_max_grid(int mt, int num_sms) {
   const int nb = (mt == 1) ? std::min(max_blocks_for<1, double>(), max_blocks_for<1, float>())
                            : std::min(max_blocks_for<8, double>(), max_blocks_for<8, float>());
   const int g = (nb >= 1) ? num_sms : 0;
-  return g > kThreads ? kThreads : g;
+  return g > kMaxThreads ? kMaxThreads : g;
 }
 
 cudaError_t launch_solver(const SolverArgs& a, int mt, int grid, cudaStream_t st) {

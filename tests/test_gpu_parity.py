@@ -127,6 +127,37 @@ def test_level_op_matches_oracle(fd_case, k):
     h.close()
 
 
+@pytest.mark.parametrize("k,prec", [(0, 0), (1, 0), (1, 1), (0, 2)])
+def test_level_op_block_matches_exact(fd_case, k, prec):
+    """Multi-right-hand-side OP (the refinement's solver tiles): 11 columns =
+    one full tile of 8 and a ragged tile of 3; FP64 (prec 0), FP32 PCG inside
+    FP64 refinement on a coarse level (1) and FP32 level-0 CG with FP64
+    reliable updates (2).  Each column must meet the same bound as the
+    single-vector OP."""
+    A, D = fd_case
+    if k > D.K:
+        pytest.skip("level absent")
+    h = _handle(A, n_coarse=60)
+    n, m, tol = D.N(k), 11, 1e-11
+    X = np.random.default_rng(40 + k).standard_normal((m, n))
+    Y = torch.zeros((m, n), dtype=torch.float64, device="cuda")
+    its = h.level_op_block(k, _dev(X), Y, tol, precision=prec)
+    assert len(its) == m and min(its) > 0
+    Ad = D.A(k).toarray()
+    rhs = X.T if k == 0 else D.M(k) @ X.T
+    exact = np.linalg.solve(Ad, rhs)
+    cond = np.linalg.cond(Ad)
+    Yg = Y.cpu().numpy().T
+    for c in range(m):
+        assert np.linalg.norm(Yg[:, c] - exact[:, c]) <= 10 * cond * tol * np.linalg.norm(exact[:, c]), c
+    if prec == 0:  # the same iteration as the single-vector OP, column by column
+        for c in (0, m - 1):
+            ctr = OS.Counters()
+            OS.op(D.A(k), D.M(k), X[c], tol, ctr=ctr)
+            assert abs(its[c] - ctr.pcg_iters) <= max(2, 0.05 * ctr.pcg_iters)
+    h.close()
+
+
 @pytest.mark.parametrize("k", [1, 2])
 def test_level_bsolve_matches_oracle(fd_case, k):
     A, D = fd_case
