@@ -234,6 +234,34 @@ void mmd_free(mmd_handle* h);
 const char* mmd_strerror(int code);
 const char* mmd_last_error(void);
 
+/* ---- a solve that allocates nothing ----
+ * The paper has no counterpart of this entry point; it exists for callers
+ * that must not allocate device memory during a call: services that reserve
+ * all GPU memory at start-up and treat a later cudaMalloc as a failure, loops
+ * with latency budgets that cannot absorb the synchronisation an allocation
+ * may cause, or frameworks that give the library only inputs and outputs.
+ *
+ * x = A^{-1} b by plain conjugate gradients (x0 = 0, stop at
+ * ||b - A x||_2 <= tol ||b||_2 or max_iter), the same iteration the library
+ * applies as Operator OP on level 0.  A is a device CSR (A->on_device = 1,
+ * full symmetric storage, SPD); b and x are device vectors of length A->n.
+ * All working memory (three vectors, reduction partials, barrier counter)
+ * is a fixed array inside the library of about 8 MB per GPU, held from the
+ * first load until the process exits, so n is limited to MMD_NOALLOC_MAX_N;
+ * larger n returns MMD_EINVAL with a message.  The call makes no cudaMalloc
+ * or cudaFree and calls no allocating library routine.
+ * The first call on a device (with that device current) looks up the array's
+ * device address once; make that first call before any stream capture.
+ * Every call reuses the same array and keeps nothing from the last one:
+ * before its kernel it clears, on its stream, what must start at zero (the
+ * barrier counter and the status word); calls that can run concurrently on
+ * the GPU (unordered streams) race on the array, so order them.  iters may be NULL.  Returns MMD_OK, MMD_EINVAL,
+ * MMD_ENOCONV (max_iter reached, x holds the last iterate), MMD_ENOTSPD,
+ * MMD_ETIMEOUT or MMD_ECUDA. */
+#define MMD_NOALLOC_MAX_N 262144
+int mmd_cg_solve_noalloc(const mmd_csr* A, const double* b, double* x, double tol, int max_iter, int64_t* iters,
+                         void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,8 +86,11 @@ SIGNATURES = {
     "mmd_free": (None, [C.c_void_p]),
     "mmd_strerror": (C.c_char_p, [C.c_int]),
     "mmd_last_error": (C.c_char_p, []),
+    "mmd_cg_solve_noalloc": (C.c_int, [C.POINTER(mmd_csr), C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                                       C.POINTER(C.c_int64), C.c_void_p]),
 }
 
+MMD_NOALLOC_MAX_N = 262144
 
 _lib = None
 
