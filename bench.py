@@ -48,6 +48,8 @@ WORKLOAD = {"workload": "torus_knn_200k", "n": 200000, "k": 10, "N": 500, "tol":
 SAMPLE = {"npts": 5000, "N": 20, "tol": 1e-8}  # bounded oracle sample of the same workload kind
 FALLBACK_HBM = 6800.0
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_all": 2}  # MMD_FP64, MMD_MIXED, MMD_MIXED_ALL
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64
+TRAFFIC_PER_LAUNCH = None  # DRAM bytes per solver launch from an ncu capture of the current kernel, when taken
 
 
 def peaks():
@@ -228,9 +230,11 @@ def gpu_arm(args, rank, world):
     # roofline of the solver kernel
     pcg_ms = sum(s["pcg_ms"] for s in stats)
     pcg_bytes = sum(s["pcg_bytes"] for s in stats)
+    pcg_flops = sum(s["pcg_flops"] for s in stats)
     pcg_launches = sum(s["pcg_launches"] for s in stats)
     peak, src = peaks()
-    achieved = (pcg_bytes / (pcg_ms / 1e3) / 1e9) if pcg_ms > 0 else None
+    gbs = (pcg_bytes / (pcg_ms / 1e3) / 1e9) if pcg_ms > 0 else None
+    tflops = (pcg_flops / (pcg_ms / 1e3) / 1e12) if pcg_ms > 0 else None
     st0 = stats[-1]
     spmv = spmv_bench(G, W, torch, sptr, peak)
     out = {
@@ -248,12 +252,17 @@ def gpu_arm(args, rank, world):
         "e2e": {"value": world * N / e2e_s, "unit": "eigenpairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "includes": "mmd_build from host CSR + eig_leftmost to host"},
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
-        "roofline": {"kernel": "solve_kernel (persistent CG/PCG)", "bound": "hbm", "achieved": achieved,
-                     "peak": peak, "peak_source": src, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "launches": pcg_launches, "share_of_step": pcg_ms / max(ms_local, 1e-9),
-                     "note": "solver matrices are L2-resident across iterations; algorithmic bytes per iteration "
-                             "12 nnz + 4 n (matrix) + 72 n per column (vectors)"},
+        "roofline": {"kernel": "solve_kernel (persistent CG/PCG)", "bound": "alu", "achieved": tflops,
+                     "peak": FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 dense FP64 (no measured FP64 peak)",
+                     "unit": "TFLOP/s", "frac": (tflops / FP64_PEAK_TFLOPS) if tflops else None,
+                     "traffic": TRAFFIC_PER_LAUNCH, "launches": pcg_launches,
+                     "share_of_step": pcg_ms / max(ms_local, 1e-9),
+                     "note": "FP64 issue bound: the level matrices (30 MB at level 0) stay in L2 across "
+                             "iterations; algorithmic flops per column-iteration 2 nnz(A) + 10 n (+ 2 nnz(M) + 10 n "
+                             "per inner iteration)",
+                     "hbm_view": {"achieved": gbs, "peak": peak, "peak_source": src, "unit": "GB/s",
+                                  "frac": (gbs / peak) if gbs else None,
+                                  "bytes": "12 nnz + 4 n per iteration (matrix) + 72 n per column (vectors)"}},
         "spmv": spmv,
         "clocks": clocks,
     }
@@ -319,7 +328,8 @@ def dist_max(v, world):
 def kernel_case(which: str):
     """Small fixed launches for ncu captures: 'op' = three Operator OP solves on
     level 0 of the torus 200k workload (one solver launch each), 'block' =
-    three 8-column OP solves there (the refinement's tile), 'spmv' = three
+    three 8-column OP solves there (the refinement's tile), 'eig' = one full
+    eig_leftmost of the workload (the launch list of a step), 'spmv' = three
     FP64 SpMVs on the 128^3 operator."""
     import torch
 
@@ -333,6 +343,12 @@ def kernel_case(which: str):
         y = torch.empty_like(x)
         its = [h.level_op(0, x, y, 1e-6) for _ in range(3)]
         print(json.dumps({"kernel_case": "op", "iters": its}))
+    elif which == "eig":
+        A = W.torus_knn(WORKLOAD["n"], k=WORKLOAD["k"], seed=W.BASE_SEED + 1)
+        h = G.MMD(A.rowptr, A.col, A.val)
+        st = h.eig_leftmost(WORKLOAD["N"], WORKLOAD["tol"], allow_noconv=True)[2]
+        print(json.dumps({"kernel_case": "eig", "kernel_launches": st["kernel_launches"],
+                          "n_converged": st["n_converged"]}))
     elif which == "block":
         A = W.torus_knn(WORKLOAD["n"], k=WORKLOAD["k"], seed=W.BASE_SEED + 1)
         h = G.MMD(A.rowptr, A.col, A.val, k_max=1)
@@ -362,7 +378,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp64")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other precision")
-    ap.add_argument("--kernel-case", choices=["op", "block", "spmv"], default=None)
+    ap.add_argument("--kernel-case", choices=["op", "block", "eig", "spmv"], default=None)
     args = ap.parse_args()
     if args.oracle_worker:
         oracle_sample_worker(args.oracle_worker)

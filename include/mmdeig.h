@@ -117,6 +117,7 @@ typedef struct {
   int64_t pcg_launches;
   double pcg_ms;        /* sum of event-timed durations */
   double pcg_bytes;     /* algorithmic bytes moved by those launches */
+  double pcg_flops;     /* algorithmic floating-point operations of those launches */
   int64_t fp64_finishes; /* MMD_MIXED_ALL: level-0 CG columns FP32 left unconverged, finished in FP64 */
   double t_level_ms[16]; /* wall time per level k (coarsest solve; refinement + extension) */
 } mmd_eig_stats;

@@ -46,6 +46,7 @@ class mmd_eig_stats(C.Structure):
                 ("n_levels", C.c_int), ("n_converged", C.c_int), ("norm_A", C.c_double),
                 ("max_rel_residual", C.c_double), ("mu1", C.c_double), ("t_total_ms", C.c_double),
                 ("pcg_launches", C.c_int64), ("pcg_ms", C.c_double), ("pcg_bytes", C.c_double),
+                ("pcg_flops", C.c_double),
                 ("fp64_finishes", C.c_int64), ("t_level_ms", C.c_double * 16)]
 
     def as_dict(self):

@@ -392,6 +392,12 @@ struct Ctx {
           bytes += (double)inn * (mb * zM / std::max(mc, 1) + 7.5 * vb * nn);
         }
         S.pcg_bytes += bytes;
+        // algorithmic flops: per column-iteration one SpMV (2 nnz) and the
+        // CG vector work (two dot products, three axpy: 10 n); mode 2 adds
+        // the segment projection (4 n); per inner iteration the same on M
+        double flops = (double)itsum * (2.0 * zA + (mode == 2 ? 14.0 : 10.0) * nn);
+        if (mode == 1) flops += (double)inn * (2.0 * (double)L.M.nnz + 10.0 * nn);
+        S.pcg_flops += flops;
       }
     }
   }
