@@ -100,13 +100,14 @@ static int upload_csr(const HCSR& A, DCSR& D) {
   int mx = 0;
   for (int64_t i = 0; i < A.nrows; ++i) mx = std::max(mx, A.rowptr[i + 1] - A.rowptr[i]);
   D.max_row = mx;
-  // SELL-32: rows sorted by length (descending, stable) inside windows of 256,
+  // SELL-32: rows sorted by length (descending, stable) inside windows of 1024,
   // slices of 32 rows stored column-major, padded with zeros (column = row).
   const int64_t n = A.nrows, ns = (n + 31) / 32;
   std::vector<int32_t> order(n);
   for (int64_t i = 0; i < n; ++i) order[i] = (int32_t)i;
-  for (int64_t w0 = 0; w0 < n; w0 += 256) {
-    const int64_t w1 = std::min<int64_t>(n, w0 + 256);
+  constexpr int64_t kSigma = 1024;  // torus kNN 200k: 1.2% padding (256: 4.2%, 32: 29%)
+  for (int64_t w0 = 0; w0 < n; w0 += kSigma) {
+    const int64_t w1 = std::min<int64_t>(n, w0 + kSigma);
     std::stable_sort(order.begin() + w0, order.begin() + w1, [&](int32_t a, int32_t b) {
       return (A.rowptr[a + 1] - A.rowptr[a]) > (A.rowptr[b + 1] - A.rowptr[b]);
     });

@@ -63,6 +63,19 @@ struct Sh {
   long long it[MT], iit[MT];
 };
 
+// Work split: block b owns the contiguous share [n b / G, n (b + 1) / G) of
+// the rows (or segments, or SELL slices); its threads (warps, for slices)
+// stride through it.  Every block gets within one unit of the same amount,
+// where a grid-wide stride gave the first blocks a whole extra round (n =
+// 200k rows on 152 x 1024 threads: 2048 rows on some SMs, 1024 on others).
+__device__ __forceinline__ int64_t share_lo(int64_t n) { return n * blockIdx.x / gridDim.x; }
+__device__ __forceinline__ int64_t share_hi(int64_t n) { return n * (blockIdx.x + 1) / gridDim.x; }
+#define FOR_BLOCK_SHARE(i, n) \
+  for (int64_t i = share_lo(n) + threadIdx.x, i##_end = share_hi(n); i < i##_end; i += blockDim.x)
+#define FOR_BLOCK_SLICES(sl, ns) \
+  for (int64_t sl = share_lo(ns) + (threadIdx.x >> 5), sl##_end = share_hi(ns); sl < sl##_end; \
+       sl += (blockDim.x >> 5))
+
 // Per-thread partial sums of the block, [MT][threads] doubles of dynamic
 // shared memory (8 KB for one column, 32 KB for eight).
 extern __shared__ double g_part[];
@@ -114,64 +127,109 @@ __device__ void write_partials(double* red, int slot, int m, const T* acc, Sh<MT
   }
 }
 
-// Y(:,c) = A X(:,c) for columns with mask[c] (SELL-32, one row per lane);
-// optionally dacc[c] += W(row,c) * Y(row,c).  The entry loop is unrolled by 4
-// so the loads of four entries are in flight before their gathers.
+// Vector layouts: the caller's b and x are column-major (element (i, c) at
+// i + c ld); the solver's own vectors r, p, q, z (and the inner ones) are
+// interleaved, element (i, c) at i MT + c, so the gather of X(j, :) in the
+// SpMV is one contiguous MT-value load instead of MT scattered ones.
+template <int MT>
+__device__ __forceinline__ int64_t wix(int64_t i, int c) {
+  return i * MT + c;
+}
+
+// The MT values X(j, 0..MT-1) of an interleaved vector (16-byte loads).
 template <int MT, typename T>
-__device__ __forceinline__ void spmv_cols(const Sell& A, const T* __restrict__ X, T* __restrict__ Y, int64_t ld,
+__device__ __forceinline__ void load_row(const T* __restrict__ X, int64_t j, T* v) {
+  if constexpr (MT == 1) {
+    v[0] = X[j];
+  } else if constexpr (sizeof(T) == 8) {
+    const double2* q = reinterpret_cast<const double2*>(X + j * MT);
+#pragma unroll
+    for (int h = 0; h < MT / 2; ++h) {
+      const double2 t = q[h];
+      v[2 * h] = t.x;
+      v[2 * h + 1] = t.y;
+    }
+  } else {
+    const float4* q = reinterpret_cast<const float4*>(X + j * MT);
+#pragma unroll
+    for (int h = 0; h < MT / 4; ++h) {
+      const float4 t = q[h];
+      v[4 * h] = t.x;
+      v[4 * h + 1] = t.y;
+      v[4 * h + 2] = t.z;
+      v[4 * h + 3] = t.w;
+    }
+  }
+}
+
+// Y(:,c) = A X(:,c) for columns with mask[c] (SELL-32, one row per lane);
+// optionally dacc[c] += W(row,c) * Y(row,c).  Y and W are interleaved; X is
+// interleaved (XI) or the caller's column-major x (stride ld).  The entry
+// loop is unrolled by 4 so the loads of four entries are in flight before
+// their gathers.
+template <int MT, typename T, bool XI>
+__device__ __forceinline__ void spmv_cols(const Sell& A, const T* __restrict__ X, int64_t ld, T* __restrict__ Y,
                                           int m, const int* mask, const T* __restrict__ W, T* dacc) {
   const T* __restrict__ vals = (sizeof(T) == 8) ? (const T*)A.val : (const T*)A.val32;
   const int lane = threadIdx.x & 31;
-  const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   int msk[MT];
 #pragma unroll
   for (int c = 0; c < MT; ++c) msk[c] = (c < m) && mask[c];
-  for (int64_t sl = gw; sl < A.nslices; sl += nw) {
+  auto gather = [&](int64_t jj, T* xv) {
+    if constexpr (XI) {
+      load_row<MT, T>(X, jj, xv);
+    } else {
+#pragma unroll
+      for (int c = 0; c < MT; ++c) xv[c] = msk[c] ? X[jj + c * ld] : T(0);
+    }
+  };
+  FOR_BLOCK_SLICES(sl, A.nslices) {
     const int32_t base = A.ptr[sl] + lane, len = A.len[sl];
     const int32_t row = A.row[sl * 32 + lane];
     T acc[MT];
 #pragma unroll
     for (int c = 0; c < MT; ++c) acc[c] = T(0);
     int32_t k = 0;
-    for (; k + 4 <= len; k += 4) {
-      T a[4];
-      int64_t j[4];
+    constexpr int U = (MT == 1) ? 4 : 2;  // entries in flight (register budget)
+    for (; k + U <= len; k += U) {
+      T a[U];
+      int64_t j[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < U; ++u) {
         a[u] = vals[base + (k + u) * 32];
         j[u] = A.col[base + (k + u) * 32];
       }
+      T xv[U][MT];
 #pragma unroll
-      for (int c = 0; c < MT; ++c)
-        if (msk[c]) {
-          T xv[4];
+      for (int u = 0; u < U; ++u) gather(j[u], xv[u]);
 #pragma unroll
-          for (int u = 0; u < 4; ++u) xv[u] = X[j[u] + c * ld];
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-          for (int u = 0; u < 4; ++u) acc[c] = fma(a[u], xv[u], acc[c]);
-        }
+        for (int c = 0; c < MT; ++c)
+          if (msk[c]) acc[c] = fma(a[u], xv[u][c], acc[c]);
     }
     for (; k < len; ++k) {
-      const T a = vals[base + k * 32];
-      const int64_t j = A.col[base + k * 32];
+      const T av = vals[base + k * 32];
+      const int64_t jj = A.col[base + k * 32];
+      T xv[MT];
+      gather(jj, xv);
 #pragma unroll
       for (int c = 0; c < MT; ++c)
-        if (msk[c]) acc[c] = fma(a, X[j + c * ld], acc[c]);
+        if (msk[c]) acc[c] = fma(av, xv[c], acc[c]);
     }
     if (row >= 0) {
 #pragma unroll
       for (int c = 0; c < MT; ++c)
         if (msk[c]) {
-          Y[row + c * ld] = acc[c];
-          if (W) dacc[c] = fma(W[row + c * ld], acc[c], dacc[c]);
+          Y[wix<MT>(row, c)] = acc[c];
+          if (W) dacc[c] = fma(W[wix<MT>(row, c)], acc[c], dacc[c]);
         }
     }
   }
 }
 
 template <int MT, typename T>
-__device__ bool inner_cg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr) {
+__device__ bool inner_cg(const SolverArgs& a, Sh<MT>& s) {
   // z = M^{-1} r for active columns, CG to relative residual itol (zero start).
   T* const r = (T*)a.r;
   T* const z = (T*)a.z;
@@ -179,7 +237,7 @@ __device__ bool inner_cg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nt
   T* const ip = (T*)a.ip;
   T* const iq = (T*)a.iq;
   const int m = a.m;
-  const int64_t n = a.n, ld = a.ld;
+  const int64_t n = a.n;
   T acc[MT];
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
     s.iact[c] = s.act[c] && s.rr[c] > 0.0;
@@ -188,13 +246,13 @@ __device__ bool inner_cg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nt
     s.iit[c] = 0;
   }
   __syncthreads();
-  for (int64_t i = tid; i < n; i += nthr)
+  FOR_BLOCK_SHARE(i, n)
     _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
       if (s.act[c]) {
-        const T rv = r[i + c * ld];
-        z[i + c * ld] = T(0);
-        ir[i + c * ld] = rv;
-        ip[i + c * ld] = rv;
+        const T rv = r[wix<MT>(i, c)];
+        z[wix<MT>(i, c)] = T(0);
+        ir[wix<MT>(i, c)] = rv;
+        ip[wix<MT>(i, c)] = rv;
       }
   if (!grid_sync(a.bar)) return false;
   for (int j = 1; j <= a.imaxit; ++j) {
@@ -203,7 +261,7 @@ __device__ bool inner_cg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nt
     if (!any) break;
 #pragma unroll
     for (int c = 0; c < MT; ++c) acc[c] = T(0);
-    spmv_cols<MT, T>(a.M, ip, iq, ld, m, s.iact, ip, acc);
+    spmv_cols<MT, T, true>(a.M, ip, 0, iq, m, s.iact, ip, acc);
     write_partials<MT, T>(a.red, 2, m, acc, s);
     if (!grid_sync(a.bar)) return false;
     reduce_slot<MT>(a.red, 2, m, s.val);
@@ -211,10 +269,10 @@ __device__ bool inner_cg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nt
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < MT; ++c) acc[c] = T(0);
-    for (int64_t i = tid; i < n; i += nthr)
+    FOR_BLOCK_SHARE(i, n)
       _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
         if (s.iact[c]) {
-          const int64_t o = i + c * ld;
+          const int64_t o = wix<MT>(i, c);
           const T al = (T)s.ia[c];
           z[o] = fma(al, ip[o], z[o]);
           const T rv = fma(-al, iq[o], ir[o]);
@@ -235,10 +293,10 @@ __device__ bool inner_cg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nt
       }
     }
     __syncthreads();
-    for (int64_t i = tid; i < n; i += nthr)
+    FOR_BLOCK_SHARE(i, n)
       _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
         if (s.iact[c]) {
-          const int64_t o = i + c * ld;
+          const int64_t o = wix<MT>(i, c);
           ip[o] = fma((T)s.ia[c], ip[o], ir[o]);
         }
     if (!grid_sync(a.bar)) return false;
@@ -256,7 +314,7 @@ __device__ bool inner_cg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nt
 // iterates as Hestenes-Stiefel CG in exact arithmetic.
 // On entry r = b - A x0 is complete and s.rr = r^T r, s.act, s.bn are set.
 template <int MT, typename T>
-__device__ bool cgcg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr) {
+__device__ bool cgcg(const SolverArgs& a, Sh<MT>& s) {
   T* const r = (T*)a.r;
   T* const p = (T*)a.p;
   T* const x = (T*)a.x;
@@ -272,7 +330,7 @@ __device__ bool cgcg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr) 
     // w = A r, delta = r^T w
 #pragma unroll
     for (int c = 0; c < MT; ++c) acc[c] = T(0);
-    spmv_cols<MT, T>(a.A, r, w, ld, m, s.act, r, acc);
+    spmv_cols<MT, T, true>(a.A, r, 0, w, m, s.act, r, acc);
     write_partials<MT, T>(a.red, 0, m, acc, s);
     if (!grid_sync(a.bar)) return false;
     reduce_slot<MT>(a.red, 0, m, s.val);
@@ -299,17 +357,17 @@ __device__ bool cgcg(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr) 
 #pragma unroll
     for (int c = 0; c < MT; ++c) acc[c] = T(0);
     const bool first = (it == 1);
-    for (int64_t i = tid; i < n; i += nthr)
+    FOR_BLOCK_SHARE(i, n)
       _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
         if (s.act[c]) {
-          const int64_t o = i + c * ld;
+          const int64_t o = wix<MT>(i, c), ox = i + c * ld;
           const T be = (T)s.val2[c], al = (T)s.alpha[c];
           const T rv0 = r[o];
           const T pv = first ? rv0 : fma(be, p[o], rv0);
           const T svv = first ? w[o] : fma(be, sv[o], w[o]);
           p[o] = pv;
           sv[o] = svv;
-          x[o] = fma(al, pv, x[o]);
+          x[ox] = fma(al, pv, x[ox]);
           const T rv = fma(-al, svv, rv0);
           r[o] = rv;
           acc[c] = fma(rv, rv, acc[c]);
@@ -338,9 +396,7 @@ __device__ void reliable_residual(const SolverArgs& a, const int* mask, T* r32, 
   const int m = a.m;
   const int64_t ld = a.ld;
   const int lane = threadIdx.x & 31;
-  const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t sl = gw; sl < A.nslices; sl += nw) {
+  FOR_BLOCK_SLICES(sl, A.nslices) {
     const int32_t base = A.ptr[sl] + lane, len = A.len[sl];
     const int32_t row = A.row[sl * 32 + lane];
     double ax[MT];
@@ -358,7 +414,7 @@ __device__ void reliable_residual(const SolverArgs& a, const int* mask, T* r32, 
       for (int c = 0; c < MT; ++c)
         if (c < m && mask[c]) {
           const double rv = a.b64[row + c * ld] - ax[c];
-          r32[row + c * ld] = (T)rv;
+          r32[wix<MT>(row, c)] = (T)rv;
           acc[c] = fma(rv, rv, acc[c]);
         }
     }
@@ -378,7 +434,7 @@ __device__ void reliable_residual(const SolverArgs& a, const int* mask, T* r32, 
 // u_32 ||A||, as for the 1e-6-shifted Laplacians -- and the caller finishes
 // it with FP64 CG from the current x.
 template <int MT, typename T>
-__device__ bool cg_rel(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr) {
+__device__ bool cg_rel(const SolverArgs& a, Sh<MT>& s) {
   T* const r = (T*)a.r;
   T* const p = (T*)a.p;
   T* const q = (T*)a.q;
@@ -393,14 +449,14 @@ __device__ bool cg_rel(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr
     dacc[c] = 0.0;
   }
   if (!a.x0)
-    for (int64_t i = tid; i < n; i += nthr)
+    FOR_BLOCK_SHARE(i, n)
       _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) a.x64[i + c * ld] = 0.0;
   if (!grid_sync(a.bar)) return false;
   reliable_residual<MT, T>(a, all1, r, dacc);
   write_partials<MT, double>(a.red, 1, m, dacc, s);
 #pragma unroll
   for (int c = 0; c < MT; ++c) dacc[c] = 0.0;
-  for (int64_t i = tid; i < n; i += nthr)
+  FOR_BLOCK_SHARE(i, n)
     _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) dacc[c] = fma(a.b64[i + c * ld], a.b64[i + c * ld], dacc[c]);
   write_partials<MT, double>(a.red, 0, m, dacc, s);
   if (!grid_sync(a.bar)) return false;
@@ -417,9 +473,9 @@ __device__ bool cg_rel(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr
     s.stag[c] = 0;
   }
   __syncthreads();
-  for (int64_t i = tid; i < n; i += nthr)
+  FOR_BLOCK_SHARE(i, n)
     _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
-      if (s.act[c]) p[i + c * ld] = r[i + c * ld];
+      if (s.act[c]) p[wix<MT>(i, c)] = r[wix<MT>(i, c)];
   if (!grid_sync(a.bar)) return false;
   for (int it = 1; it <= a.maxit; ++it) {
     int any = 0;
@@ -428,7 +484,7 @@ __device__ bool cg_rel(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr
     // q = A p, p^T q
 #pragma unroll
     for (int c = 0; c < MT; ++c) acc[c] = T(0);
-    spmv_cols<MT, T>(a.A, p, q, ld, m, s.act, p, acc);
+    spmv_cols<MT, T, true>(a.A, p, 0, q, m, s.act, p, acc);
     write_partials<MT, T>(a.red, 0, m, acc, s);
     if (!grid_sync(a.bar)) return false;
     reduce_slot<MT>(a.red, 0, m, s.val);
@@ -449,12 +505,12 @@ __device__ bool cg_rel(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr
     // x += alpha p (FP64), r -= alpha q, r^T r
 #pragma unroll
     for (int c = 0; c < MT; ++c) acc[c] = T(0);
-    for (int64_t i = tid; i < n; i += nthr)
+    FOR_BLOCK_SHARE(i, n)
       _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
         if (s.act[c]) {
-          const int64_t o = i + c * ld;
+          const int64_t o = wix<MT>(i, c), ox = i + c * ld;
           const T al = (T)s.alpha[c];
-          a.x64[o] = fma(s.alpha[c], (double)p[o], a.x64[o]);
+          a.x64[ox] = fma(s.alpha[c], (double)p[o], a.x64[ox]);
           const T rv = fma(-al, q[o], r[o]);
           r[o] = rv;
           acc[c] = fma(rv, rv, acc[c]);
@@ -510,10 +566,10 @@ __device__ bool cg_rel(const SolverArgs& a, Sh<MT>& s, int64_t tid, int64_t nthr
       }
     }
     __syncthreads();
-    for (int64_t i = tid; i < n; i += nthr)
+    FOR_BLOCK_SHARE(i, n)
       _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
         if (s.act[c]) {
-          const int64_t o = i + c * ld;
+          const int64_t o = wix<MT>(i, c);
           p[o] = fma((T)s.val[c], p[o], r[o]);
         }
     if (!grid_sync(a.bar)) return false;
@@ -533,10 +589,8 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
   T* const z = (T*)a.z;
   const int m = a.m;
   const int64_t n = a.n, ld = a.ld;
-  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t nthr = int64_t(gridDim.x) * blockDim.x;
   if (a.mode == 0 && a.b64) {
-    if (!cg_rel<MT, T>(a, s, tid, nthr)) return;
+    if (!cg_rel<MT, T>(a, s)) return;
     if (blockIdx.x == 0 && threadIdx.x < m) {
       a.it_out[threadIdx.x] = s.it[threadIdx.x];
       a.conv[threadIdx.x] = s.ok[threadIdx.x];
@@ -549,7 +603,7 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
   for (int c = 0; c < MT; ++c) all1[c] = 1;
   // ---- set-up: r = b - A x0 (or b), norms
   if (a.x0) {
-    spmv_cols<MT, T>(a.A, x, q, ld, m, all1, nullptr, nullptr);
+    spmv_cols<MT, T, false>(a.A, x, ld, q, m, all1, nullptr, nullptr);
     if (!grid_sync(a.bar)) return;
   }
 #pragma unroll
@@ -558,34 +612,34 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
     // r = P (b - A x0) per segment: a right-hand side projected once by the
     // caller keeps a rounding-level component along phi, as large as its
     // projected part when b was nearly parallel to phi; CG could not remove it
-    for (int64_t sg = tid; sg < a.nseg; sg += nthr) {
+    FOR_BLOCK_SHARE(sg, a.nseg) {
       const int32_t s0 = a.seg_ptr[sg], s1 = a.seg_ptr[sg + 1];
       _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) {
         T t = T(0);
         for (int32_t i = s0; i < s1; ++i) {
-          const int64_t o = i + c * ld;
-          t = fma((T)a.phi[i], a.x0 ? b[o] - q[o] : b[o], t);
+          const int64_t o = i + c * ld, w = wix<MT>(i, c);
+          t = fma((T)a.phi[i], a.x0 ? b[o] - q[w] : b[o], t);
         }
         for (int32_t i = s0; i < s1; ++i) {
-          const int64_t o = i + c * ld;
+          const int64_t o = i + c * ld, w = wix<MT>(i, c);
           const T bv = b[o];
-          const T rv = fma(-(T)a.phi[i], t, a.x0 ? bv - q[o] : bv);
+          const T rv = fma(-(T)a.phi[i], t, a.x0 ? bv - q[w] : bv);
           if (!a.x0) x[o] = T(0);
-          r[o] = rv;
+          r[w] = rv;
           acc[c] = fma(bv, bv, acc[c]);
           acc2[c] = fma(rv, rv, acc2[c]);
         }
       }
     }
   } else {
-    for (int64_t i = tid; i < n; i += nthr)
+    FOR_BLOCK_SHARE(i, n)
       _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) {
-        const int64_t o = i + c * ld;
+        const int64_t o = i + c * ld, w = wix<MT>(i, c);
         const T bv = b[o];
         T rv = bv;
-        if (a.x0) rv -= q[o];
+        if (a.x0) rv -= q[w];
         else x[o] = T(0);
-        r[o] = rv;
+        r[w] = rv;
         acc[c] = fma(bv, bv, acc[c]);
         acc2[c] = fma(rv, rv, acc2[c]);
       }
@@ -602,11 +656,11 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
     s.it[c] = 0;
   }
   __syncthreads();
-  for (int64_t i = tid; i < n; i += nthr)  // zero right-hand sides give x = 0
+  FOR_BLOCK_SHARE(i, n)  // zero right-hand sides give x = 0
     _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
       if (s.bn[c] == 0.0) x[i + c * ld] = T(0);
   if (a.mode == 0) {
-    if (!cgcg<MT, T>(a, s, tid, nthr)) return;
+    if (!cgcg<MT, T>(a, s)) return;
     if (blockIdx.x == 0 && threadIdx.x < m) {
       a.it_out[threadIdx.x] = s.it[threadIdx.x];
       a.conv[threadIdx.x] = s.act[threadIdx.x] ? 0 : 1;
@@ -615,13 +669,13 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
   }
   T* zv = r;
   if (a.mode == 1) {
-    if (!inner_cg<MT, T>(a, s, tid, nthr)) return;
+    if (!inner_cg<MT, T>(a, s)) return;
     zv = z;
 #pragma unroll
     for (int c = 0; c < MT; ++c) acc[c] = T(0);
-    for (int64_t i = tid; i < n; i += nthr)
+    FOR_BLOCK_SHARE(i, n)
       _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
-        if (s.act[c]) acc[c] = fma(r[i + c * ld], z[i + c * ld], acc[c]);
+        if (s.act[c]) acc[c] = fma(r[wix<MT>(i, c)], z[wix<MT>(i, c)], acc[c]);
     write_partials<MT, T>(a.red, 0, m, acc, s);
     if (!grid_sync(a.bar)) return;
     reduce_slot<MT>(a.red, 0, m, s.rz);
@@ -629,9 +683,9 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
     if (threadIdx.x < m) s.rz[threadIdx.x] = s.rr[threadIdx.x];
     __syncthreads();
   }
-  for (int64_t i = tid; i < n; i += nthr)
+  FOR_BLOCK_SHARE(i, n)
     _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
-      if (s.act[c]) p[i + c * ld] = zv[i + c * ld];
+      if (s.act[c]) p[wix<MT>(i, c)] = zv[wix<MT>(i, c)];
   if (!grid_sync(a.bar)) return;
 
   for (int it = 1; it <= a.maxit; ++it) {
@@ -641,7 +695,7 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
     // q = A p, p^T q
 #pragma unroll
     for (int c = 0; c < MT; ++c) acc[c] = T(0);
-    spmv_cols<MT, T>(a.A, p, q, ld, m, s.act, p, acc);
+    spmv_cols<MT, T, true>(a.A, p, 0, q, m, s.act, p, acc);
     write_partials<MT, T>(a.red, 0, m, acc, s);
     if (!grid_sync(a.bar)) return;
     reduce_slot<MT>(a.red, 0, m, s.val);
@@ -662,17 +716,17 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
 #pragma unroll
     for (int c = 0; c < MT; ++c) acc[c] = T(0);
     if (a.mode == 2) {
-      for (int64_t sg = tid; sg < a.nseg; sg += nthr) {
+      FOR_BLOCK_SHARE(sg, a.nseg) {
         const int32_t s0 = a.seg_ptr[sg], s1 = a.seg_ptr[sg + 1];
         _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) {
           if (!s.act[c]) continue;
           const T al = (T)s.alpha[c];
           T t = T(0);
-          for (int32_t i = s0; i < s1; ++i) t = fma((T)a.phi[i], q[i + c * ld], t);
+          for (int32_t i = s0; i < s1; ++i) t = fma((T)a.phi[i], q[wix<MT>(i, c)], t);
           for (int32_t i = s0; i < s1; ++i) {
-            const int64_t o = i + c * ld;
+            const int64_t o = wix<MT>(i, c), ox = i + c * ld;
             const T qv = fma(-(T)a.phi[i], t, q[o]);
-            x[o] = fma(al, p[o], x[o]);
+            x[ox] = fma(al, p[o], x[ox]);
             const T rv = fma(-al, qv, r[o]);
             r[o] = rv;
             acc[c] = fma(rv, rv, acc[c]);
@@ -680,12 +734,12 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
         }
       }
     } else {
-      for (int64_t i = tid; i < n; i += nthr)
+      FOR_BLOCK_SHARE(i, n)
         _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
           if (s.act[c]) {
-            const int64_t o = i + c * ld;
+            const int64_t o = wix<MT>(i, c), ox = i + c * ld;
             const T al = (T)s.alpha[c];
-            x[o] = fma(al, p[o], x[o]);
+            x[ox] = fma(al, p[o], x[ox]);
             const T rv = fma(-al, q[o], r[o]);
             r[o] = rv;
             acc[c] = fma(rv, rv, acc[c]);
@@ -710,13 +764,13 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
         s.rr[c] = s.val2[c];
       }
       __syncthreads();
-      if (!inner_cg<MT, T>(a, s, tid, nthr)) return;
+      if (!inner_cg<MT, T>(a, s)) return;
 #pragma unroll
       for (int c = 0; c < MT; ++c) acc[c] = acc2[c] = T(0);
-      for (int64_t i = tid; i < n; i += nthr)
+      FOR_BLOCK_SHARE(i, n)
         _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
           if (s.act[c]) {
-            const int64_t o = i + c * ld;
+            const int64_t o = wix<MT>(i, c);
             acc[c] = fma(r[o], z[o], acc[c]);
             acc2[c] = fma(z[o], q[o], acc2[c]);
           }
@@ -743,10 +797,10 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
       }
     }
     __syncthreads();
-    for (int64_t i = tid; i < n; i += nthr)
+    FOR_BLOCK_SHARE(i, n)
       _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
         if (s.act[c]) {
-          const int64_t o = i + c * ld;
+          const int64_t o = wix<MT>(i, c);
           p[o] = fma((T)s.alpha[c], p[o], zv[o]);
         }
     if (!grid_sync(a.bar)) return;
