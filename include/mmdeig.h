@@ -184,8 +184,9 @@ int eig_leftmost(mmd_handle* h, int N, double tol, const mmd_eig_opts* opts,
  * use of Algorithm 6: one decomposition per graph).  hs[i], N[i], lambda[i],
  * V[i] and stats[i] (stats may be NULL) are those of problem i; tol and opts
  * are shared (opts->stream is ignored).  The problems run concurrently on
- * `streams` non-blocking CUDA streams (<= 0: 8), one host thread per stream,
- * problem i on stream i mod streams.  Each stream's cooperative solver
+ * `streams` non-blocking CUDA streams (<= 0: 8), one host thread per stream;
+ * the largest problems (n N) start first and each stream takes the next
+ * problem when it is free.  Each stream's cooperative solver
  * launches use at most (SM count / streams) blocks, so the concurrent grids
  * are co-resident.  The handles must be distinct.  Returns MMD_OK, or the first failing problem's code (all
  * problems are still attempted; mmd_last_error names the problem). */

@@ -173,12 +173,13 @@ class MMD:
         return g
 
 
-def eig_leftmost_batched(handles, N, tol: float, streams: int = 8, **opts):
+def eig_leftmost_batched(handles, N, tol: float, streams: int = 8, allow_noconv: bool = False, **opts):
     """N[i] smallest eigenpairs of each handle's matrix, the problems solved
     concurrently on ``streams`` CUDA streams (eig_leftmost_batched).
 
     ``N``: int or one int per handle.  Returns lists (lam_i, V_i, stats_i),
-    host numpy arrays."""
+    host numpy arrays.  With ``allow_noconv`` an iteration cap in some problem
+    returns the best pairs found (stats_i["n_converged"] tells which)."""
     lib = _lib.load()
     cnt = len(handles)
     Ns = [int(N)] * cnt if np.isscalar(N) else [int(x) for x in N]
@@ -193,7 +194,8 @@ def eig_leftmost_batched(handles, N, tol: float, streams: int = 8, **opts):
     vp = (C.c_void_p * cnt)(*[a.ctypes.data for a in Vs])
     st = (_lib.mmd_eig_stats * cnt)()
     rc = lib.eig_leftmost_batched(hs, cnt, na, tol, C.byref(o), lp, vp, 0, st, streams)
-    _lib.check(rc, "eig_leftmost_batched")
+    if rc != _lib.MMD_OK and not (allow_noconv and rc == _lib.MMD_ENOCONV):
+        _lib.check(rc, "eig_leftmost_batched")
     return [(lams[i], Vs[i].T, st[i].as_dict()) for i in range(cnt)]
 
 

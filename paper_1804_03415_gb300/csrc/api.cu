@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -477,6 +478,14 @@ int eig_leftmost_batched(mmd_handle* const* hs, int count, const int* N, double 
     }
   std::vector<int> rcs(count, MMD_OK);
   std::vector<std::string> msgs(count);
+  // largest problems first, each stream taking the next one when it is free
+  // (longest-processing-time-first list scheduling)
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (int64_t)hs[a]->A0.nrows * N[a] > (int64_t)hs[b]->A0.nrows * N[b];
+  });
+  std::atomic<int> next{0};
   std::vector<std::thread> th;
   for (int t = 0; t < ns; ++t)
     th.emplace_back([&, t]() {
@@ -484,7 +493,8 @@ int eig_leftmost_batched(mmd_handle* const* hs, int count, const int* N, double 
       set_coop_grid_cap(cap);
       mmd_eig_opts ot = o;
       ot.stream = st[t];
-      for (int i = t; i < count; i += ns) {
+      for (int q = next++; q < count; q = next++) {
+        const int i = order[q];
         rcs[i] = run_eig(hs[i], N[i], tol, ot, lambda[i], V[i], outputs_on_device, stats ? &stats[i] : nullptr);
         if (rcs[i] != MMD_OK) msgs[i] = mmd_last_error();
       }

@@ -54,7 +54,7 @@ constexpr int kMaxThreads = 1024;
 
 template <int MT>
 struct Sh {
-  double quart[MT * 4];  // block reduction: per-warp sums, up to 4 warps per column
+  double quart[2 * MT * 4];  // block reduction: per-warp sums, up to 4 warps per value
   double bn[MT], rz[MT], rr[MT], alpha[MT], val[MT], val2[MT];
   double irr[MT], irn0[MT], ia[MT];
   int act[MT], iact[MT];
@@ -76,54 +76,65 @@ __device__ __forceinline__ int64_t share_hi(int64_t n) { return n * (blockIdx.x 
   for (int64_t sl = share_lo(ns) + (threadIdx.x >> 5), sl##_end = share_hi(ns); sl < sl##_end; \
        sl += (blockDim.x >> 5))
 
-// Per-thread partial sums of the block, [MT][threads] doubles of dynamic
-// shared memory (8 KB for one column, 32 KB for eight).
+// Per-thread partial sums of the block, [2 MT][threads] doubles of dynamic
+// shared memory (16 KB for one column, 64 KB for eight).
 extern __shared__ double g_part[];
 
-// partial sums red[slot][c][block] -> dst[c] (shared) in every block; warp c
-// sums column c, so the columns are reduced on different SM sub-partitions
+// partial sums red[slot][c][block] -> dst[c] (shared) in every block, and
+// with dst2 also red[slot2][c][block] -> dst2[c]; warp v sums value v, so the
+// values are reduced on different SM sub-partitions
 template <int MT>
-__device__ void reduce_slot(const double* red, int slot, int m, double* dst) {
+__device__ __forceinline__ void reduce_slot(const double* red, int slot, int m, double* dst, int slot2 = 0,
+                                            double* dst2 = nullptr) {
   const int G = gridDim.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (w < m) {
-    const double* p = red + (size_t(slot) * MT + w) * G;
+  const int nv = dst2 ? 2 * m : m;
+  if (w < nv) {
+    const int c = w < m ? w : w - m;
+    const double* p = red + (size_t(w < m ? slot : slot2) * MT + c) * G;
     double t = 0.0;
     for (int b = lane; b < G; b += 32) t += p[b];
     t = warp_sum(t);
-    if (lane == 0) dst[w] = t;
+    if (lane == 0) (w < m ? dst : dst2)[c] = t;
   }
   __syncthreads();
 }
 
-// Block sums of acc[c], c < m, written to red[slot][c][blockIdx].  Every
-// thread stores its partials; then wpc warps per column (4 for one or two
-// columns, 2 for up to four, else 1) each add a contiguous share with all 32
-// lanes busy and finish with one shuffle tree.  Consecutive warps sit on
-// different SM sub-partitions, so the FP64 adds of the columns proceed in
-// parallel instead of queueing behind one warp.  Fixed order: deterministic.
+// Block sums of acc[c], c < m, written to red[slot][c][blockIdx] (and of
+// acc2[c] to red[slot2][c][blockIdx]).  Every thread stores its partials;
+// then wpc warps per value (4 for one or two values, 2 for up to four, else
+// 1) each add a contiguous share with all 32 lanes busy and finish with one
+// shuffle tree.  Consecutive warps sit on different SM sub-partitions, so the
+// FP64 adds of the values proceed in parallel instead of queueing behind one
+// warp.  Fixed order: deterministic.
 template <int MT, typename T>
-__device__ void write_partials(double* red, int slot, int m, const T* acc, Sh<MT>& s) {
+__device__ __forceinline__ void write_partials(double* red, int slot, int m, const T* acc, Sh<MT>& s,
+                                               const T* acc2 = nullptr, int slot2 = 0) {
   constexpr int NT = threads_for<MT>();
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int nv = acc2 ? 2 * m : m;
 #pragma unroll
   for (int c = 0; c < MT; ++c)
-    if (c < m) g_part[c * NT + tid] = (double)acc[c];
+    if (c < m) {
+      g_part[c * NT + tid] = (double)acc[c];
+      if (acc2) g_part[(m + c) * NT + tid] = (double)acc2[c];
+    }
   __syncthreads();
-  const int wpc = (m <= 2) ? 4 : (m <= 4 ? 2 : 1);
+  const int wpc = (nv <= 2) ? 4 : (nv <= 4 ? 2 : 1);
   const int span = NT / wpc;
-  if (w < m * wpc) {
-    const int c = w / wpc, q = w - c * wpc;
-    const double* p = g_part + c * NT + q * span;
+  if (w < nv * wpc) {
+    const int v = w / wpc, q = w - v * wpc;
+    const double* p = g_part + v * NT + q * span;
     double t = 0.0;
     for (int i = lane; i < span; i += 32) t += p[i];
     t = warp_sum(t);
-    if (lane == 0) s.quart[c * 4 + q] = t;
+    if (lane == 0) s.quart[v * 4 + q] = t;
   }
   __syncthreads();
-  if (tid < m) {
+  if (tid < nv) {
     double t = s.quart[tid * 4];
     for (int q = 1; q < wpc; ++q) t += s.quart[tid * 4 + q];
-    red[(size_t(slot) * MT + tid) * gridDim.x + blockIdx.x] = t;
+    const int c = tid < m ? tid : tid - m;
+    red[(size_t(tid < m ? slot : slot2) * MT + c) * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -163,13 +174,15 @@ __device__ __forceinline__ void load_row(const T* __restrict__ X, int64_t j, T* 
 }
 
 // Y(:,c) = A X(:,c) for columns with mask[c] (SELL-32, one row per lane);
-// optionally dacc[c] += W(row,c) * Y(row,c).  Y and W are interleaved; X is
+// optionally dacc[c] += W(row,c) * Y(row,c) (and dacc2[c] += W(row,c)^2).
+// Y and W are interleaved; X is
 // interleaved (XI) or the caller's column-major x (stride ld).  The entry
 // loop is unrolled by 4 so the loads of four entries are in flight before
 // their gathers.
 template <int MT, typename T, bool XI>
 __device__ __forceinline__ void spmv_cols(const Sell& A, const T* __restrict__ X, int64_t ld, T* __restrict__ Y,
-                                          int m, const int* mask, const T* __restrict__ W, T* dacc) {
+                                          int m, const int* mask, const T* __restrict__ W, T* dacc,
+                                          T* dacc2 = nullptr) {
   const T* __restrict__ vals = (sizeof(T) == 8) ? (const T*)A.val : (const T*)A.val32;
   const int lane = threadIdx.x & 31;
   int msk[MT];
@@ -222,7 +235,11 @@ __device__ __forceinline__ void spmv_cols(const Sell& A, const T* __restrict__ X
       for (int c = 0; c < MT; ++c)
         if (msk[c]) {
           Y[wix<MT>(row, c)] = acc[c];
-          if (W) dacc[c] = fma(W[wix<MT>(row, c)], acc[c], dacc[c]);
+          if (W) {
+            const T wv = W[wix<MT>(row, c)];
+            dacc[c] = fma(wv, acc[c], dacc[c]);
+            if (dacc2) dacc2[c] = fma(wv, wv, dacc2[c]);
+          }
         }
     }
   }
@@ -309,9 +326,12 @@ __device__ bool inner_cg(const SolverArgs& a, Sh<MT>& s) {
   return true;
 }
 
-// Mode 0: CG in the Chronopoulos-Gear form (one fused reduction of r^T r and
-// r^T A r per iteration, so two grid barriers instead of three); same
-// iterates as Hestenes-Stiefel CG in exact arithmetic.
+// Mode 0: CG in the Chronopoulos-Gear form: r^T r and r^T A r are both
+// formed in the SpMV pass (w = A r), so an iteration has one reduction round
+// (block sums, grid barrier, partials) and one plain grid barrier before the
+// next SpMV; same iterates as Hestenes-Stiefel CG in exact arithmetic.  The
+// convergence test sees r^T r of the last update in the next pass, so a
+// converged column has done one SpMV more than it needed.
 // On entry r = b - A x0 is complete and s.rr = r^T r, s.act, s.bn are set.
 template <int MT, typename T>
 __device__ bool cgcg(const SolverArgs& a, Sh<MT>& s) {
@@ -322,40 +342,44 @@ __device__ bool cgcg(const SolverArgs& a, Sh<MT>& s) {
   T* const sv = (T*)a.q;
   const int m = a.m;
   const int64_t n = a.n, ld = a.ld;
-  T acc[MT];
-  for (int it = 1; it <= a.maxit; ++it) {
+  T acc[MT], acc2[MT];
+  for (int it = 1;; ++it) {
     int any = 0;
     _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) any |= s.act[c];
     if (!any) break;
-    // w = A r, delta = r^T w
+    // w = A r; delta = r^T w, gamma = r^T r
 #pragma unroll
-    for (int c = 0; c < MT; ++c) acc[c] = T(0);
-    spmv_cols<MT, T, true>(a.A, r, 0, w, m, s.act, r, acc);
-    write_partials<MT, T>(a.red, 0, m, acc, s);
+    for (int c = 0; c < MT; ++c) acc[c] = acc2[c] = T(0);
+    spmv_cols<MT, T, true>(a.A, r, 0, w, m, s.act, r, acc, acc2);
+    write_partials<MT, T>(a.red, 0, m, acc, s, acc2, 1);
     if (!grid_sync(a.bar)) return false;
-    reduce_slot<MT>(a.red, 0, m, s.val);
+    reduce_slot<MT>(a.red, 0, m, s.val, 1, s.val2);
     if (threadIdx.x < m) {
       const int c = threadIdx.x;
       if (s.act[c]) {
-        const double g = s.rr[c], dl = s.val[c];
-        double be = 0.0, den = dl;
-        if (it > 1) {
-          be = g / s.rz[c];
-          den = dl - be * g / s.alpha[c];
+        const double g = s.val2[c], dl = s.val[c];
+        if (it > 1 && g <= a.tol * a.tol * s.bn[c] * s.bn[c]) {
+          s.act[c] = 0;  // converged after update it - 1
+        } else if (it <= a.maxit) {
+          double be = 0.0, den = dl;
+          if (it > 1) {
+            be = g / s.rz[c];
+            den = dl - be * g / s.alpha[c];
+          }
+          if (!(den > 0.0)) {
+            s.act[c] = 0;
+            if (blockIdx.x == 0) atomicExch(a.bar.status, (int)DEV_NOTSPD);
+          }
+          s.rz[c] = g;
+          s.alpha[c] = g / den;
+          s.val2[c] = be;
+          s.it[c] = it;
         }
-        if (!(den > 0.0)) {
-          s.act[c] = 0;
-          if (blockIdx.x == 0) atomicExch(a.bar.status, (int)DEV_NOTSPD);
-        }
-        s.rz[c] = g;
-        s.alpha[c] = g / den;
-        s.val2[c] = be;
       }
     }
     __syncthreads();
-    // p = r + beta p, s = w + beta s, x += alpha p, r -= alpha s, gamma = r^T r
-#pragma unroll
-    for (int c = 0; c < MT; ++c) acc[c] = T(0);
+    if (it > a.maxit) break;  // columns still active report no convergence
+    // p = r + beta p, s = w + beta s, x += alpha p, r -= alpha s
     const bool first = (it == 1);
     FOR_BLOCK_SHARE(i, n)
       _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m)
@@ -368,22 +392,9 @@ __device__ bool cgcg(const SolverArgs& a, Sh<MT>& s) {
           p[o] = pv;
           sv[o] = svv;
           x[ox] = fma(al, pv, x[ox]);
-          const T rv = fma(-al, svv, rv0);
-          r[o] = rv;
-          acc[c] = fma(rv, rv, acc[c]);
+          r[o] = fma(-al, svv, rv0);
         }
-    write_partials<MT, T>(a.red, 1, m, acc, s);
     if (!grid_sync(a.bar)) return false;
-    reduce_slot<MT>(a.red, 1, m, s.val);
-    if (threadIdx.x < m) {
-      const int c = threadIdx.x;
-      if (s.act[c]) {
-        s.it[c] = it;
-        s.rr[c] = s.val[c];
-        if (sqrt(s.val[c]) <= a.tol * s.bn[c]) s.act[c] = 0;
-      }
-    }
-    __syncthreads();
   }
   return true;
 }
@@ -814,7 +825,7 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
 
 template <int MT>
 constexpr size_t dyn_smem() {
-  return sizeof(double) * size_t(MT) * threads_for<MT>();
+  return sizeof(double) * 2 * size_t(MT) * threads_for<MT>();
 }
 
 // the 64 KB of the eight-column instance exceed the default 48 KB window
