@@ -49,7 +49,9 @@ SAMPLE = {"npts": 5000, "N": 20, "tol": 1e-8}  # bounded oracle sample of the sa
 FALLBACK_HBM = 6800.0
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_all": 2}  # MMD_FP64, MMD_MIXED, MMD_MIXED_ALL
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64
-TRAFFIC_PER_LAUNCH = None  # DRAM bytes per solver launch from an ncu capture of the current kernel, when taken
+# DRAM bytes per launch of the solver, from an ncu capture of solve_kernel<1, double> on the level-0
+# matrix of this workload (bench.py --kernel-case op); the matrix is read once per launch
+TRAFFIC_PER_LAUNCH = 33.66e6
 
 
 def peaks():

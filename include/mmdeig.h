@@ -73,12 +73,14 @@ typedef struct {
 typedef struct {
   int s_max;      /* pass-1 patch size cap; joins allowed up to 2*s_max (default 8) */
   int omega_max;  /* row cap of a psi support neighbourhood (default 256) */
-  int loc_radius; /* 0: support = own patch, 1: plus neighbouring patches (default 1) */
+  int loc_radius; /* 0: support = own patch, r >= 1: plus r rings of neighbouring patches (default 1) */
   int n_coarse;   /* stop when N^(k) <= n_coarse (default 300) */
   int k_max;      /* maximum number of levels (default 8) */
   int device;     /* 1: upload the levels to the current CUDA device (default);
                      0: host-only handle (inspection with mmd_level_info only) */
   int threads;    /* host threads for the build, 0 = all cores */
+  double peel;    /* > 0: split weakly attached rows off a patch while its 1/lambda_2
+                     exceeds peel x the median over patches (bounds eps(P)); 0 = off */
 } mmd_build_opts;
 
 /* Solver options (Section 6 parameter rules). */

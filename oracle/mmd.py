@@ -48,7 +48,8 @@ from workloads import CSR
 class BuildOpts:
     s_max: int = 8  # seed patch size cap (pass 1); pass-2 joins allowed while size < 2 s_max
     omega_max: int = 256  # row cap of a localisation neighbourhood Omega_j
-    loc_radius: int = 1  # 0: Omega_j = P_j, 1: P_j plus neighbouring patches
+    loc_radius: int = 1  # 0: Omega_j = P_j, r >= 1: P_j plus r rings of neighbouring patches
+    peel: float = 0.0  # > 0: split off weakly attached rows while 1/lambda_2(patch) > peel * median
     n_coarse: int = 300
     k_max: int = 8
     not_psd_tol: float = 1e-10  # interior energy is "not PSD" if lambda_min < -tol * max|lambda|
@@ -161,6 +162,63 @@ def partition(rowptr: np.ndarray, col: np.ndarray, n: int, s_max: int):
     return patch_of.astype(np.int32), patch_ptr, patch_rows
 
 
+def _inv_lambda2(A: sp.csr_matrix, rowabs: np.ndarray, S: np.ndarray, not_psd_tol: float) -> float:
+    """1 / lambda_2 of the patch energy of rows S (interior energy, closed
+    energy when that is not PSD), the patch's share of eps(P) (Section 2.2)."""
+    AS = A[S][:, S].toarray()
+    inside = np.abs(AS).sum(axis=1)
+    E = AS - np.diag(rowabs[S] - inside)
+    w = np.linalg.eigvalsh(E)
+    if w[0] < -not_psd_tol * np.max(np.abs(w)):
+        w = np.linalg.eigvalsh(AS)
+    return 1.0 / w[1]
+
+
+def peel(A: sp.csr_matrix, patch_of, patch_ptr, patch_rows, mult: float, not_psd_tol: float):
+    """Bound eps(P) by splitting weakly attached rows off their patches.
+
+    eps(P) is a maximum over patches, so one row that hangs on its patch by
+    small weights sets it for the whole level.  With cap = mult x the median
+    of 1/lambda_2 over patches of two or more rows (lower median), each patch
+    in id order loses, while 1/lambda_2 > cap, the row with the smallest
+    interior weight sum_{u in S, u != v} |a_vu| (ties: lowest row); every
+    removed row becomes a singleton patch, numbered after all existing
+    patches in removal order.  Sums run over the CSR row in column order.
+    """
+    if mult <= 0:
+        return patch_of, patch_ptr, patch_rows
+    n = A.shape[0]
+    rowabs = np.array([sum(abs(float(v)) for v in A.data[A.indptr[r]:A.indptr[r + 1]]) for r in range(n)])
+    npatch = len(patch_ptr) - 1
+    inv = sorted(_inv_lambda2(A, rowabs, patch_rows[patch_ptr[j]:patch_ptr[j + 1]], not_psd_tol)
+                 for j in range(npatch) if patch_ptr[j + 1] - patch_ptr[j] > 1)
+    if not inv:
+        return patch_of, patch_ptr, patch_rows
+    cap = mult * inv[(len(inv) - 1) // 2]
+    new_of = np.array(patch_of, dtype=np.int64)
+    nxt = npatch
+    for j in range(npatch):
+        S = [int(r) for r in patch_rows[patch_ptr[j]:patch_ptr[j + 1]]]
+        while len(S) > 1 and _inv_lambda2(A, rowabs, np.array(S), not_psd_tol) > cap:
+            inS = set(S)
+            best, bw = -1, 0.0
+            for v in S:  # ascending rows: the first minimum is the lowest row
+                t = 0.0
+                for k in range(A.indptr[v], A.indptr[v + 1]):
+                    c = int(A.indices[k])
+                    if c != v and c in inS:
+                        t += abs(float(A.data[k]))
+                if best < 0 or t < bw:
+                    best, bw = v, t
+            S.remove(best)
+            new_of[best] = nxt
+            nxt += 1
+    order = np.lexsort((np.arange(n), new_of))
+    ptr = np.zeros(nxt + 1, dtype=np.int32)
+    ptr[1:] = np.cumsum(np.bincount(new_of, minlength=nxt))
+    return new_of.astype(np.int32), ptr, order.astype(np.int32)
+
+
 # --------------------------------------------------------------------------
 # 2-4. local bases
 def _sign_fix(v: np.ndarray) -> np.ndarray:
@@ -185,7 +243,7 @@ def local_bases(A: sp.csr_matrix, patch_ptr, patch_rows, not_psd_tol: float):
         outside = rowabs[S] - inside  # sum_{j not in S} |a_ij|
         E = AS - np.diag(outside)
         w, V = np.linalg.eigh(E)
-        if w[0] < -not_psd_tol * np.max(np.abs(w)):
+        if len(S) > 1 and w[0] < -not_psd_tol * np.max(np.abs(w)):  # a singleton's phi is 1 either way
             used_closed += 1
             E = AS
             w, V = np.linalg.eigh(E)
@@ -204,14 +262,26 @@ def local_bases(A: sp.csr_matrix, patch_ptr, patch_rows, not_psd_tol: float):
 # --------------------------------------------------------------------------
 # 5. localised Psi
 def neighbourhoods(A: sp.csr_matrix, patch_of, patch_ptr, patch_rows, omega_max: int, loc_radius: int):
-    """Omega_j = P_j plus whole neighbouring patches, integer-only selection.
+    """Omega_j = P_j plus whole patches in rings around it, integer-only selection.
 
-    Neighbouring patches are ranked by the number of pattern entries (r, c),
-    r in P_j, c in P_i, c != r (descending; ties: lowest patch id) and added
-    while the row count stays <= omega_max.
+    Ring 1: the patches holding neighbours of P_j, ranked by the number of
+    pattern entries (r, c), r in P_j, c in P_i, c != r (descending; ties:
+    lowest patch id).  Ring t >= 2: the patches adjacent to a patch taken in
+    ring t - 1 that no earlier ring offered, ascending id.  A patch is added
+    while the row count stays <= omega_max (a patch that does not fit is
+    skipped and the next one tried).
     """
     npatch = len(patch_ptr) - 1
     rowptr, col = A.indptr, A.indices
+    adj = None
+    if loc_radius >= 2:
+        adj = [set() for _ in range(npatch)]
+        for r in range(A.shape[0]):
+            pr = int(patch_of[r])
+            for c in col[rowptr[r]:rowptr[r + 1]]:
+                pc = int(patch_of[c])
+                if pc != pr:
+                    adj[pr].add(pc)
     optr = [0]
     orows = []
     for j in range(npatch):
@@ -228,11 +298,24 @@ def neighbourhoods(A: sp.csr_matrix, patch_of, patch_ptr, patch_rows, omega_max:
                     if p != j:
                         counts[p] = counts.get(p, 0) + 1
             ranked = sorted(counts.items(), key=lambda t: (-t[1], t[0]))
+            seen = {j} | set(counts)
+            ring = []
             for p, _ in ranked:
                 sz = int(patch_ptr[p + 1] - patch_ptr[p])
                 if total + sz <= omega_max:
                     chosen.append(p)
+                    ring.append(p)
                     total += sz
+            for _ in range(2, loc_radius + 1):
+                cand = sorted({q for p in ring for q in adj[p]} - seen)
+                seen.update(cand)
+                ring = []
+                for p in cand:
+                    sz = int(patch_ptr[p + 1] - patch_ptr[p])
+                    if total + sz <= omega_max:
+                        chosen.append(p)
+                        ring.append(p)
+                        total += sz
         rows = np.sort(np.concatenate([patch_rows[patch_ptr[p]:patch_ptr[p + 1]] for p in chosen]))
         orows.append(rows)
         optr.append(optr[-1] + len(rows))
@@ -316,6 +399,7 @@ def build_level(A: sp.csr_matrix, Mprev, opts: BuildOpts) -> Level:
     A.sort_indices()
     n_fine = A.shape[0]
     patch_of, patch_ptr, patch_rows = partition(A.indptr, A.indices, n_fine, opts.s_max)
+    patch_of, patch_ptr, patch_rows = peel(A, patch_of, patch_ptr, patch_rows, opts.peel, opts.not_psd_tol)
     phi, uhat, eps, delta, used_closed = local_bases(A, patch_ptr, patch_rows, opts.not_psd_tol)
     optr, orows = neighbourhoods(A, patch_of, patch_ptr, patch_rows, opts.omega_max, opts.loc_radius)
     Psi = localized_psi(A, patch_of, patch_ptr, patch_rows, phi, optr, orows)

@@ -205,6 +205,102 @@ void partition(const HCSR& A, int s_max, std::vector<int32_t>& patch_of, std::ve
   for (int64_t i = 0; i < n; ++i) patch_rows[fill[po[i]]++] = (int32_t)i;
 }
 
+// 1 / lambda_2 of the patch energy of rows S (ascending): interior energy
+// A[S,S] - diag(sum of |a_rc| outside S), or A[S,S] when that is not PSD --
+// the patch's share of eps(P) (Section 2.2).
+double inv_lambda2(const HCSR& A, const std::vector<double>& rowabs, const std::vector<int32_t>& S) {
+  const int s = (int)S.size();
+  std::vector<double> AS(size_t(s) * s, 0.0), E, w, V;
+  for (int x = 0; x < s; ++x) {
+    const int r = S[x];
+    for (int32_t k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k) {
+      auto it = std::lower_bound(S.begin(), S.end(), A.col[k]);
+      if (it != S.end() && *it == A.col[k]) AS[size_t(x) * s + (it - S.begin())] = A.val[k];
+    }
+  }
+  E = AS;
+  for (int x = 0; x < s; ++x) {
+    double inside = 0;
+    for (int y = 0; y < s; ++y) inside += std::fabs(AS[size_t(x) * s + y]);
+    E[size_t(x) * s + x] -= rowabs[S[x]] - inside;
+  }
+  jacobi_eig(s, E, w, V);
+  double wmax = 0;
+  for (double t : w) wmax = std::max(wmax, std::fabs(t));
+  if (w[0] < -1e-10 * wmax) {
+    E = AS;
+    jacobi_eig(s, E, w, V);
+  }
+  return 1.0 / w[1];
+}
+
+// Bound eps(P) by splitting weakly attached rows off their patches (build
+// option peel > 0).  eps(P) is a maximum over patches, so one row hanging on
+// its patch by small weights sets it for the whole level.  With cap = peel x
+// the lower median of 1/lambda_2 over patches of two or more rows, each patch
+// in id order loses, while 1/lambda_2 > cap, the row with the smallest
+// interior weight sum_{u in S, u != v} |a_vu| (ties: lowest row); removed
+// rows become singleton patches numbered after the existing ones in removal
+// order.  Sums run over the CSR row in column order.
+void peel_patches(const HCSR& A, double mult, std::vector<int32_t>& patch_of, std::vector<int32_t>& patch_ptr,
+                  std::vector<int32_t>& patch_rows, int nthreads) {
+  if (!(mult > 0)) return;
+  const int64_t n = A.nrows, np = (int64_t)patch_ptr.size() - 1;
+  std::vector<double> rowabs(n, 0.0);
+  for (int64_t r = 0; r < n; ++r) {
+    double t = 0;
+    for (int32_t k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k) t += std::fabs(A.val[k]);
+    rowabs[r] = t;
+  }
+  std::vector<double> inv(np, -1.0);
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
+  for (int64_t j = 0; j < np; ++j) {
+    if (patch_ptr[j + 1] - patch_ptr[j] < 2) continue;
+    std::vector<int32_t> S(patch_rows.begin() + patch_ptr[j], patch_rows.begin() + patch_ptr[j + 1]);
+    inv[j] = inv_lambda2(A, rowabs, S);
+  }
+  std::vector<double> sorted;
+  for (double t : inv)
+    if (t >= 0) sorted.push_back(t);
+  if (sorted.empty()) return;
+  std::sort(sorted.begin(), sorted.end());
+  const double cap = mult * sorted[(sorted.size() - 1) / 2];
+  // each patch is peeled independently; removals are numbered in patch order
+  std::vector<std::vector<int32_t>> removed(np);
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+  for (int64_t j = 0; j < np; ++j) {
+    if (!(inv[j] > cap)) continue;
+    std::vector<int32_t> S(patch_rows.begin() + patch_ptr[j], patch_rows.begin() + patch_ptr[j + 1]);
+    while (S.size() > 1 && inv_lambda2(A, rowabs, S) > cap) {
+      int32_t best = -1;
+      double bw = 0;
+      for (int32_t v : S) {
+        double t = 0;
+        for (int32_t k = A.rowptr[v]; k < A.rowptr[v + 1]; ++k) {
+          const int32_t c = A.col[k];
+          if (c != v && std::binary_search(S.begin(), S.end(), c)) t += std::fabs(A.val[k]);
+        }
+        if (best < 0 || t < bw) {
+          best = v;
+          bw = t;
+        }
+      }
+      S.erase(std::find(S.begin(), S.end(), best));
+      removed[j].push_back(best);
+    }
+  }
+  int32_t nxt = (int32_t)np;
+  for (int64_t j = 0; j < np; ++j)
+    for (int32_t v : removed[j]) patch_of[v] = nxt++;
+  const int64_t np2 = nxt;
+  patch_ptr.assign(np2 + 1, 0);
+  for (int64_t i = 0; i < n; ++i) ++patch_ptr[patch_of[i] + 1];
+  for (int64_t p = 0; p < np2; ++p) patch_ptr[p + 1] += patch_ptr[p];
+  std::vector<int32_t> fill(patch_ptr.begin(), patch_ptr.end() - 1);
+  patch_rows.resize(n);
+  for (int64_t i = 0; i < n; ++i) patch_rows[fill[patch_of[i]]++] = (int32_t)i;
+}
+
 // ------------------------------------------------------------ 2-4. bases
 struct PatchOut {
   double eps = 0, delta = 0;
@@ -247,7 +343,7 @@ void local_bases(const HCSR& A, const std::vector<int32_t>& patch_ptr, const std
     jacobi_eig(s, E, w, V);
     double wmax = 0;
     for (double t : w) wmax = std::max(wmax, std::fabs(t));
-    if (w[0] < -1e-10 * wmax) {
+    if (s > 1 && w[0] < -1e-10 * wmax) {  // a singleton's phi is 1 either way
       po[j].closed = 1;
       E = AS;
       jacobi_eig(s, E, w, V);
@@ -298,6 +394,21 @@ void neighbourhoods(const HCSR& A, const std::vector<int32_t>& patch_of, const s
                     std::vector<int32_t>& optr, std::vector<int32_t>& orows, int nthreads) {
   const int64_t np = (int64_t)patch_ptr.size() - 1;
   std::vector<std::vector<int32_t>> per(np);
+  // patch adjacency (sorted, unique), for rings beyond the first
+  std::vector<std::vector<int32_t>> adj;
+  if (loc_radius >= 2) {
+    adj.assign(np, {});
+    for (int64_t r = 0; r < A.nrows; ++r)
+      for (int32_t k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k) {
+        const int32_t pr = patch_of[r], pc = patch_of[A.col[k]];
+        if (pc != pr) adj[pr].push_back(pc);
+      }
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads)
+    for (int64_t p = 0; p < np; ++p) {
+      std::sort(adj[p].begin(), adj[p].end());
+      adj[p].erase(std::unique(adj[p].begin(), adj[p].end()), adj[p].end());
+    }
+  }
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
   for (int64_t j = 0; j < np; ++j) {
     std::vector<int32_t> chosen{(int32_t)j};
@@ -321,11 +432,34 @@ void neighbourhoods(const HCSR& A, const std::vector<int32_t>& patch_of, const s
         a = b;
       }
       std::sort(ranked.begin(), ranked.end());
+      std::vector<int32_t> seen{(int32_t)j}, ring;
       for (const auto& t : ranked) {
+        seen.push_back(t.second);
         const int sz = patch_ptr[t.second + 1] - patch_ptr[t.second];
         if (total + sz <= omega_max) {
           chosen.push_back(t.second);
+          ring.push_back(t.second);
           total += sz;
+        }
+      }
+      // ring t >= 2: patches adjacent to ring t - 1 not offered before, ascending
+      for (int t = 2; t <= loc_radius; ++t) {
+        std::sort(seen.begin(), seen.end());
+        std::vector<int32_t> cand;
+        for (int32_t p : ring)
+          for (int32_t q : adj[p])
+            if (!std::binary_search(seen.begin(), seen.end(), q)) cand.push_back(q);
+        std::sort(cand.begin(), cand.end());
+        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+        ring.clear();
+        for (int32_t p : cand) {
+          seen.push_back(p);
+          const int sz = patch_ptr[p + 1] - patch_ptr[p];
+          if (total + sz <= omega_max) {
+            chosen.push_back(p);
+            ring.push_back(p);
+            total += sz;
+          }
         }
       }
     }
@@ -592,6 +726,7 @@ int build_host(const mmd_csr* Ain, const mmd_build_opts* o, mmd_handle* h) {
     HLevel L;
     L.n_fine = cur->nrows;
     partition(*cur, o->s_max, L.patch_of, L.patch_ptr, L.patch_rows);
+    peel_patches(*cur, o->peel, L.patch_of, L.patch_ptr, L.patch_rows, nt);
     L.n = (int64_t)L.patch_ptr.size() - 1;
     if (L.n >= cur->nrows) break;
     bool ok = true;

@@ -66,12 +66,16 @@ def test_strerror_and_validation(pkg):
         pkg.MMD(rp2, ci[keep], va[keep], device=False)
 
 
-@pytest.mark.parametrize("case", ["fd2d_32", "torus_4000", "rgg_3000"])
-def test_host_build_matches_oracle(pkg, case):
+@pytest.mark.parametrize("case,peel,rings", [("fd2d_32", 0.0, 1), ("torus_4000", 0.0, 1), ("rgg_3000", 0.0, 1),
+                                             ("torus_4000", 3.0, 2), ("fd2d_32", 2.0, 3)])
+def test_host_build_matches_oracle(pkg, case, peel, rings):
+    """Library build vs oracle build: integer indexing bit-exact, values to
+    1e-10; also with eps-bounded patches (peel) and wider psi supports."""
     A = {"fd2d_32": lambda: W.fd2d(32, seed=3), "torus_4000": lambda: W.torus_knn(4000, seed=4),
          "rgg_3000": lambda: W.rgg(3000, seed=5)}[case]()
-    h = pkg.MMD(A.rowptr, A.col, A.val, device=False, n_coarse=50)
-    D = OM.build(A, OM.BuildOpts(n_coarse=50))
+    om = 256 if rings == 1 else 1024
+    h = pkg.MMD(A.rowptr, A.col, A.val, device=False, n_coarse=50, peel=peel, loc_radius=rings, omega_max=om)
+    D = OM.build(A, OM.BuildOpts(n_coarse=50, peel=peel, loc_radius=rings, omega_max=om))
     assert h.num_levels == D.K
     for k in range(1, D.K + 1):
         L, O = h.level(k), D.levels[k - 1]
