@@ -169,6 +169,65 @@ def test_exact_psi_compression_bound():
     assert np.linalg.eigvalsh(Psi.T @ Ad @ Psi)[-1] <= lev.delta * (1 + 1e-10)
 
 
+def test_global_support_gives_the_exact_psi():
+    """With Omega_j covering every patch (enough rings, no row cap) the
+    constrained energy minimiser is the exact Psi = A^{-1} Phi (Phi^T A^{-1} Phi)^{-1}
+    of Section 2.3 (its columns are A-orthogonal to ker Phi^T); one ring is
+    not, and the exact level's smallest eigenvalue is the closest."""
+    A = W.fd2d(10, const=True)
+    Ad = A.dense()
+    Ai = np.linalg.inv(Ad)
+    lam1 = np.linalg.eigvalsh(Ad)[0]
+    errs = []
+    for rings in (1, 2, 50):
+        D = MM.build(A, MM.BuildOpts(n_coarse=5, k_max=1, loc_radius=rings, omega_max=10**6))
+        lev = D.levels[0]
+        Phi = MM.Phi_matrix(lev).toarray()
+        exact = Ai @ Phi @ np.linalg.inv(Phi.T @ Ai @ Phi)
+        psi = lev.psi.toarray()
+        if rings == 50:
+            assert np.abs(psi - exact).max() <= 1e-10 * np.abs(exact).max()
+        w = sla.eigh(D.A(1).toarray(), D.M(1).toarray(), eigvals_only=True)
+        assert w[0] >= lam1 * (1 - 1e-12)  # Courant-Fischer: the coarse space only raises it
+        errs.append(w[0] - lam1)
+    assert errs[2] <= errs[1] <= errs[0]
+
+
+def test_peel_bounds_eps_and_keeps_a_partition():
+    """peel > 0: every patch of two or more rows ends with 1/lambda_2 <= cap
+    (cap = peel x the lower median before peeling), removed rows are
+    singleton patches numbered after the others, and the level still
+    partitions the rows (checked against dense eigenvalues of each patch)."""
+    A = W.torus_knn(1500, seed=W.BASE_SEED + 9)
+    As = A.to_scipy().tocsr()
+    Ad = A.dense()
+    absd = np.abs(Ad)
+    rowabs = absd.sum(axis=1)
+
+    def inv_l2(S):
+        AS = Ad[np.ix_(S, S)]
+        E = AS - np.diag(rowabs[S] - np.abs(AS).sum(axis=1))
+        w = np.linalg.eigvalsh(E)
+        if w[0] < -1e-10 * np.abs(w).max():
+            w = np.linalg.eigvalsh(AS)
+        return 1.0 / w[1]
+
+    po, pp, pr = MM.partition(As.indptr, As.indices, A.n, 8)
+    before = sorted(inv_l2(pr[pp[j]:pp[j + 1]]) for j in range(len(pp) - 1) if pp[j + 1] - pp[j] > 1)
+    cap = 3.0 * before[(len(before) - 1) // 2]
+    qo, qp, qr = MM.peel(As, po, pp, pr, 3.0, 1e-10)
+    npatch0 = len(pp) - 1
+    assert np.array_equal(np.sort(qr), np.arange(A.n))
+    assert np.array_equal(np.diff(qp)[npatch0:], np.ones(len(qp) - 1 - npatch0, dtype=np.int32))
+    for j in range(len(qp) - 1):
+        S = qr[qp[j]:qp[j + 1]]
+        assert np.all(qo[S] == j)
+        if len(S) > 1:
+            assert inv_l2(S) <= cap * (1 + 1e-9)
+            assert set(S) <= set(pr[pp[j]:pp[j + 1]])  # a remainder of the original patch j
+    assert max(before) > cap  # the case does peel something
+
+
 # ------------------------------------------------------------------ solvers
 def test_cg_fpcg_bsolve():
     A = W.random_spd_mmatrix(400, 6.0, 4, shift=0.1).to_scipy()
