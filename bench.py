@@ -341,7 +341,7 @@ def job_value(world: int, n_eig: int, steps: int, max_ms: float) -> float:
 def kernel_case(which: str):
     """Small fixed launches for ncu captures: 'op' = three Operator OP solves on
     level 0 of the torus 200k workload (one solver launch each), 'block' =
-    three 8-column OP solves there (the refinement's tile), 'eig' = one full
+    three 8-column OP solves there (two of the refinement's 4-column tiles each), 'eig' = one full
     eig_leftmost of the workload (the launch list of a step), 'spmv' = three
     FP64 SpMVs on the 128^3 operator."""
     import torch

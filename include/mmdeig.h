@@ -221,7 +221,7 @@ int eig_grad(mmd_handle* h, const double* dL_dlambda, const double* dL_dV, int i
  *   OP box after Algorithm 3); k = 0 uses M = I (plain CG).  iters may be NULL.
  * mmd_level_op_block: Y = OP(X) for m columns (n_k x m, column-major), the
  *   warm-start-free form of the refinement's multi-right-hand-side PCG
- *   (Algorithm 5), 8 columns per solver launch; precision as in
+ *   (Algorithm 5), 4 columns per solver launch; precision as in
  *   mmd_eig_opts; iters (m entries) may be NULL.
  * mmd_level_bsolve: x = U g where g = CG(B^(k), U^T M^(k-1) q, tol) and
  *   B^(k) = U^(k)^T A^(k-1) U^(k) (Algorithm 5, first loop); q and x are

@@ -3,8 +3,8 @@
 // by an inner CG to 0.1 eps) and of the two solves of the Eigenpair
 // Refinement (Algorithm 5: CG on B^(l) = U^T A U and the warm-started PCG).
 //
-// One cooperative launch (one block per SM: 1024 threads, 512 for eight
-// columns) runs a whole solve for m <= MT right-hand sides (column-major,
+// One cooperative launch (one 1024-thread block per SM) runs a whole solve
+// for m <= MT right-hand sides (column-major,
 // leading dimension ld).  Scalars never leave the device: each block writes its partial sums, a bounded grid barrier
 // follows, and every block then reduces the same partials in the same order,
 // so all blocks take identical decisions.
@@ -43,12 +43,13 @@ namespace mmd {
 
 namespace {
 
-// Threads per block (one block per SM): 1024 for one right-hand side; 512
-// for the eight-column tiles, whose eight accumulators per row need the 128
-// registers a thread gets at 512 threads per SM.
+// Threads per block (one block per SM).  Tiles are one or four columns
+// wide: four accumulators and their gathers fit the 64 registers a thread
+// gets at 1024 threads per SM (an eight-column tile needed 512-thread blocks
+// for its registers and cost 3% more per column-iteration).
 template <int MT>
 __host__ __device__ constexpr int threads_for() {
-  return MT == 1 ? 1024 : 512;
+  return 1024;
 }
 constexpr int kMaxThreads = 1024;
 
@@ -77,7 +78,7 @@ __device__ __forceinline__ int64_t share_hi(int64_t n) { return n * (blockIdx.x 
        sl += (blockDim.x >> 5))
 
 // Per-thread partial sums of the block, [2 MT][threads] doubles of dynamic
-// shared memory (16 KB for one column, 64 KB for eight).
+// shared memory (16 KB for one column, 64 KB for four).
 extern __shared__ double g_part[];
 
 // partial sums red[slot][c][block] -> dst[c] (shared) in every block, and
@@ -828,7 +829,7 @@ constexpr size_t dyn_smem() {
   return sizeof(double) * 2 * size_t(MT) * threads_for<MT>();
 }
 
-// the 64 KB of the eight-column instance exceed the default 48 KB window
+// the 64 KB of the four-column instance exceed the default 48 KB window
 template <int MT, typename T>
 void allow_smem() {
   static std::once_flag once;
@@ -855,12 +856,12 @@ cudaError_t launch_tpl(const SolverArgs& a, int grid, cudaStream_t st) {
 
 }  // namespace
 
-int solver_threads(int mt) { return mt == 1 ? threads_for<1>() : threads_for<8>(); }
+int solver_threads(int mt) { return mt == 1 ? threads_for<1>() : threads_for<4>(); }
 
 // One block per SM (the reductions read one partial per block, <= 1024).
 int solver_max_grid(int mt, int num_sms) {
   const int nb = (mt == 1) ? std::min(max_blocks_for<1, double>(), max_blocks_for<1, float>())
-                           : std::min(max_blocks_for<8, double>(), max_blocks_for<8, float>());
+                           : std::min(max_blocks_for<4, double>(), max_blocks_for<4, float>());
   const int g = (nb >= 1) ? num_sms : 0;
   return g > kMaxThreads ? kMaxThreads : g;
 }
@@ -868,10 +869,10 @@ int solver_max_grid(int mt, int num_sms) {
 cudaError_t launch_solver(const SolverArgs& a, int mt, int grid, cudaStream_t st) {
   if (a.fp32) {
     if (mt == 1) return launch_tpl<1, float>(a, grid, st);
-    if (mt == 8) return launch_tpl<8, float>(a, grid, st);
+    if (mt == 4) return launch_tpl<4, float>(a, grid, st);
   } else {
     if (mt == 1) return launch_tpl<1, double>(a, grid, st);
-    if (mt == 8) return launch_tpl<8, double>(a, grid, st);
+    if (mt == 4) return launch_tpl<4, double>(a, grid, st);
   }
   return cudaErrorInvalidValue;
 }
