@@ -89,3 +89,35 @@ def test_host_build_matches_oracle(pkg, case, peel, rings):
         assert abs(L["delta"] - O.delta) <= 1e-10 * O.delta
         assert L["used_closed"] == O.used_closed
     h.close()
+
+
+def test_entry_points_refuse_host_only_handles_and_bad_options(pkg):
+    """Calls that need the device levels refuse a host-only handle with
+    MMD_EINVAL (and a message) before touching any device memory; build
+    options out of range are refused too.  No GPU is used."""
+    import ctypes as C
+
+    lib = pkg._lib.load()
+    A = W.fd2d(8, seed=11)
+    h = pkg.MMD(A.rowptr, A.col, A.val, device=False, n_coarse=20)
+    lam = np.zeros(3)
+    V = np.zeros((3, A.n))
+    st = pkg._lib.mmd_eig_stats()
+    o = pkg.eig_opts()
+    assert lib.eig_leftmost(h.h, 3, 1e-8, C.byref(o), lam.ctypes.data, V.ctypes.data, 0, C.byref(st)) == \
+        pkg._lib.MMD_EINVAL
+    hs = (C.c_void_p * 1)(h.h.value)
+    na = (C.c_int * 1)(3)
+    lp = (C.c_void_p * 1)(lam.ctypes.data)
+    vp = (C.c_void_p * 1)(V.ctypes.data)
+    assert lib.eig_leftmost_batched(hs, 1, na, 1e-8, C.byref(o), lp, vp, 0, None, 2) == pkg._lib.MMD_EINVAL
+    assert b"problem 0" in lib.mmd_last_error()
+    its = (C.c_int64 * 2)()
+    assert lib.mmd_level_op_block(h.h, 0, 2, V.ctypes.data, V.ctypes.data, 1e-8, 10, its, 0, None) == \
+        pkg._lib.MMD_EINVAL
+    g = np.zeros(A.nnz)
+    assert lib.eig_grad(h.h, lam.ctypes.data, None, 0, g.ctypes.data, 0, C.byref(o)) == pkg._lib.MMD_EINVAL
+    h.close()
+    for bad in ({"peel": -1.0}, {"loc_radius": -1}, {"s_max": 0}):
+        with pytest.raises(pkg.MMDError):
+            pkg.MMD(A.rowptr, A.col, A.val, device=False, **bad)
