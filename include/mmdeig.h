@@ -73,7 +73,8 @@ typedef struct {
 typedef struct {
   int s_max;      /* pass-1 patch size cap; joins allowed up to 2*s_max (default 8) */
   int omega_max;  /* row cap of a psi support neighbourhood (default 256) */
-  int loc_radius; /* 0: support = own patch, r >= 1: plus r rings of neighbouring patches (default 1) */
+  int loc_radius; /* 0: support = own patch, r >= 1: plus r rings of neighbouring patches
+                     (default 1; r > 1 at level 1 only, deeper levels use one ring) */
   int n_coarse;   /* stop when N^(k) <= n_coarse (default 300) */
   int k_max;      /* maximum number of levels (default 8) */
   int device;     /* 1: upload the levels to the current CUDA device (default);

@@ -48,7 +48,7 @@ from workloads import CSR
 class BuildOpts:
     s_max: int = 8  # seed patch size cap (pass 1); pass-2 joins allowed while size < 2 s_max
     omega_max: int = 256  # row cap of a localisation neighbourhood Omega_j
-    loc_radius: int = 1  # 0: Omega_j = P_j, r >= 1: P_j plus r rings of neighbouring patches
+    loc_radius: int = 1  # 0: Omega_j = P_j, r >= 1: P_j plus r rings of neighbouring patches (r > 1: level 1)
     peel: float = 0.0  # > 0: split off weakly attached rows while 1/lambda_2(patch) > peel * median
     n_coarse: int = 300
     k_max: int = 8
@@ -394,14 +394,18 @@ def galerkin(Psi: sp.csr_matrix, B: sp.csr_matrix | None) -> sp.csr_matrix:
 
 
 # --------------------------------------------------------------------------
-def build_level(A: sp.csr_matrix, Mprev, opts: BuildOpts) -> Level:
+def build_level(A: sp.csr_matrix, Mprev, opts: BuildOpts, k: int = 1) -> Level:
+    """Level k from level k - 1.  Wider supports (loc_radius > 1) apply to
+    level 1 only; deeper levels use at most one ring (their Galerkin matrices
+    are dense enough that two rings reach omega_max)."""
     A = A.tocsr()
     A.sort_indices()
     n_fine = A.shape[0]
     patch_of, patch_ptr, patch_rows = partition(A.indptr, A.indices, n_fine, opts.s_max)
     patch_of, patch_ptr, patch_rows = peel(A, patch_of, patch_ptr, patch_rows, opts.peel, opts.not_psd_tol)
     phi, uhat, eps, delta, used_closed = local_bases(A, patch_ptr, patch_rows, opts.not_psd_tol)
-    optr, orows = neighbourhoods(A, patch_of, patch_ptr, patch_rows, opts.omega_max, opts.loc_radius)
+    radius = opts.loc_radius if k == 1 else min(opts.loc_radius, 1)
+    optr, orows = neighbourhoods(A, patch_of, patch_ptr, patch_rows, opts.omega_max, radius)
     Psi = localized_psi(A, patch_of, patch_ptr, patch_rows, phi, optr, orows)
     Ak = galerkin(Psi, A)
     Mk = galerkin(Psi, Mprev)
@@ -417,7 +421,7 @@ def build(A: CSR | sp.csr_matrix, opts: BuildOpts | None = None) -> MMD:
     levels = []
     cur, Mcur = A0, None
     while cur.shape[0] > opts.n_coarse and len(levels) < opts.k_max:
-        lev = build_level(cur, Mcur, opts)
+        lev = build_level(cur, Mcur, opts, len(levels) + 1)
         if lev.n >= cur.shape[0]:
             break
         levels.append(lev)

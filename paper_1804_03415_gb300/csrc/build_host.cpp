@@ -736,8 +736,11 @@ int build_host(const mmd_csr* Ain, const mmd_build_opts* o, mmd_handle* h) {
                 std::to_string(h->levels.size() + 1));
       return MMD_ENOTSPD;
     }
-    neighbourhoods(*cur, L.patch_of, L.patch_ptr, L.patch_rows, o->omega_max, o->loc_radius, L.omega_ptr,
-                   L.omega_rows, nt);
+    // wider supports at level 1 only: the Galerkin matrices of deeper levels
+    // are dense enough that two rings reach omega_max
+    const int radius = h->levels.empty() ? o->loc_radius : std::min(o->loc_radius, 1);
+    neighbourhoods(*cur, L.patch_of, L.patch_ptr, L.patch_rows, o->omega_max, radius, L.omega_ptr, L.omega_rows,
+                   nt);
     std::vector<double> psival;
     if (!localized_psi(*cur, L.patch_of, L.phi, L.patch_rows, L.omega_ptr, L.omega_rows, L.n, psival, nt)) {
       set_error("mmd_build: a neighbourhood matrix is not positive definite at level " +
