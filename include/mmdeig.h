@@ -189,10 +189,11 @@ int eig_leftmost(mmd_handle* h, int N, double tol, const mmd_eig_opts* opts,
  * are shared (opts->stream is ignored).  The problems run concurrently on
  * `streams` non-blocking CUDA streams (<= 0: 8), one host thread per stream;
  * the largest problems (n N) start first and each stream takes the next
- * problem when it is free.  Each stream's cooperative solver
- * launches use at most (SM count / streams) blocks, so the concurrent grids
- * are co-resident.  The handles must be distinct.  Returns MMD_OK, or the first failing problem's code (all
- * problems are still attempted; mmd_last_error names the problem). */
+ * problem when it is free.  Each stream's cooperative solver launches use at
+ * most (SM count / streams) blocks, so the concurrent grids are co-resident.
+ * The handles must be distinct.  Returns MMD_OK, or the first failing
+ * problem's code (all problems are still attempted; mmd_last_error names the
+ * problem). */
 int eig_leftmost_batched(mmd_handle* const* hs, int count, const int* N, double tol, const mmd_eig_opts* opts,
                          double* const* lambda, double* const* V, int outputs_on_device,
                          mmd_eig_stats* stats, int streams);
