@@ -219,6 +219,10 @@ int eig_grad(mmd_handle* h, const double* dL_dlambda, const double* dL_dV, int i
 /* Level operators on device vectors of level k, in the natural (build) order
  * of that level, for tests and kernel benchmarks.
  * mmd_level_spmv: y = A^(k) x (which = 0) or M^(k) x (which = 1, k >= 1).
+ * mmd_level_spmv_timed: the same product, computed reps times back to back
+ *   on the level's device-order copy of x; *ms = mean time of one SpMV
+ *   kernel between two events on the stream (the permutations of x and y
+ *   stay outside the timed region).
  * mmd_level_op: y = OP(x) = pcg(A^(k), M^(k) x, M^(k), 0, tol) (the Operator
  *   OP box after Algorithm 3); k = 0 uses M = I (plain CG).  iters may be NULL.
  * mmd_level_op_block: Y = OP(X) for m columns (n_k x m, column-major), the
@@ -229,6 +233,8 @@ int eig_grad(mmd_handle* h, const double* dL_dlambda, const double* dL_dV, int i
  *   B^(k) = U^(k)^T A^(k-1) U^(k) (Algorithm 5, first loop); q and x are
  *   level-(k-1) vectors, 1 <= k <= K. */
 int mmd_level_spmv(mmd_handle* h, int k, int which, const double* x, double* y, void* stream);
+int mmd_level_spmv_timed(mmd_handle* h, int k, int which, const double* x, double* y, int reps, float* ms,
+                         void* stream);
 int mmd_level_op(mmd_handle* h, int k, const double* x, double* y, double tol, int max_iter,
                  int64_t* iters, void* stream);
 int mmd_level_op_block(mmd_handle* h, int k, int m, const double* X, double* Y, double tol, int max_iter,

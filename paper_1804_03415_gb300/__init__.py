@@ -110,6 +110,13 @@ class MMD:
     def level_spmv(self, k, which, x, y, stream=0):
         _lib.check(self._lib.mmd_level_spmv(self.h, k, which, x.data_ptr(), y.data_ptr(), stream), "mmd_level_spmv")
 
+    def level_spmv_timed(self, k, which, x, y, reps=20, stream=0) -> float:
+        """y = A^(k) x (or M^(k) x) computed reps times; returns ms per SpMV kernel."""
+        ms = C.c_float(0.0)
+        _lib.check(self._lib.mmd_level_spmv_timed(self.h, k, which, x.data_ptr(), y.data_ptr(), reps, C.byref(ms),
+                                                  stream), "mmd_level_spmv_timed")
+        return float(ms.value)
+
     def level_op(self, k, x, y, tol, max_iter=20000, stream=0) -> int:
         it = C.c_int64(0)
         _lib.check(self._lib.mmd_level_op(self.h, k, x.data_ptr(), y.data_ptr(), tol, max_iter, C.byref(it), stream),

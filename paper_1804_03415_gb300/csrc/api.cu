@@ -400,6 +400,16 @@ int mmd_level_spmv(mmd_handle* h, int k, int which, const double* x, double* y, 
   return level_spmv(h, k, which, x, y, (cudaStream_t)stream);
 }
 
+int mmd_level_spmv_timed(mmd_handle* h, int k, int which, const double* x, double* y, int reps, float* ms,
+                         void* stream) {
+  if (!h || !h->on_device || k < 0 || k > (int)h->levels.size() || (which != 0 && which != 1) ||
+      (which == 1 && k == 0) || !x || !y || reps < 1 || !ms) {
+    set_error("mmd_level_spmv_timed: bad arguments");
+    return MMD_EINVAL;
+  }
+  return level_spmv_timed(h, k, which, x, y, reps, ms, (cudaStream_t)stream);
+}
+
 int mmd_level_op(mmd_handle* h, int k, const double* x, double* y, double tol, int max_iter, int64_t* iters,
                  void* stream) {
   if (!h || !h->on_device || k < 0 || k > (int)h->levels.size() || !x || !y || !(tol > 0) || max_iter < 1) {

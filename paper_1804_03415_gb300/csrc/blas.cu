@@ -54,7 +54,29 @@ __global__ void spmv_kernel(Sell A, const double* __restrict__ x, int64_t ldx, d
       const int32_t base = A.ptr[sl], len = A.len[sl];
       const int32_t row = A.row[sl * 32 + lane];
       double acc[4] = {0, 0, 0, 0};
-      for (int32_t k = 0; k < len; ++k) {
+      int32_t k = 0;
+      // four entries' loads in flight before their gathers and FMAs (the
+      // FMA order per row is unchanged: entries in CSR order)
+      for (; k + 4 <= len; k += 4) {
+        double a[4];
+        int64_t j[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int32_t o = base + (k + u) * 32 + lane;
+          a[u] = A.val[o];
+          j[u] = A.col[o];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c < mc) {
+            double xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = x[j[u] + (c0 + c) * ldx];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[c] = fma(a[u], xv[u], acc[c]);
+          }
+      }
+      for (; k < len; ++k) {
         const int32_t o = base + k * 32 + lane;
         const double a = A.val[o];
         const int64_t j = A.col[o];

@@ -891,6 +891,42 @@ int level_spmv(mmd_handle* h, int k, int which, const double* x, double* y, cuda
   return MMD_OK;
 }
 
+// reps back-to-back SpMVs on device-order vectors between two events on the
+// stream: the kernel's own time, without the permutations and the
+// synchronisation of level_spmv.
+int level_spmv_timed(mmd_handle* h, int k, int which, const double* x, double* y, int reps, float* ms,
+                     cudaStream_t st) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  try {
+    mmd_eig_opts o;
+    mmd_default_eig_opts(&o);
+    Ctx c(h, st, o);
+    const DLevel& L = h->dl[k];
+    double* a = buf<double>(c.ws, "lt_a", L.n);
+    double* b = buf<double>(c.ws, "lt_b", L.n);
+    k_gather(x, L.n, L.d_perm, L.n, 1, a, L.n, st);
+    c.spmv(k, which, a, b, 1);  // warm-up
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; ++r) c.spmv(k, which, a, b, 1);
+    CK(cudaEventRecord(e1, st));
+    k_scatter(b, L.n, L.d_perm, L.n, 1, y, L.n, st);
+    c.sync();
+    CK(cudaGetLastError());
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, e0, e1));
+    *ms = t / reps;
+  } catch (const CudaFail& f) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return f.code;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return MMD_OK;
+}
+
 int level_op(mmd_handle* h, int k, const double* x, double* y, double tol, int max_iter, int64_t* iters,
              cudaStream_t st) {
   try {

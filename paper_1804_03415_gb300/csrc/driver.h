@@ -8,6 +8,8 @@
 namespace mmd {
 
 int level_spmv(mmd_handle* h, int k, int which, const double* x, double* y, cudaStream_t st);
+int level_spmv_timed(mmd_handle* h, int k, int which, const double* x, double* y, int reps, float* ms,
+                     cudaStream_t st);
 int level_op(mmd_handle* h, int k, const double* x, double* y, double tol, int max_iter, int64_t* iters,
              cudaStream_t st);
 int level_op_block(mmd_handle* h, int k, int m, const double* x, double* y, double tol, int max_iter,

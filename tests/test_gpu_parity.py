@@ -101,6 +101,23 @@ def test_level_spmv(fd_case):
     h.close()
 
 
+def test_timed_spmv_matches_plain_spmv(fd_case):
+    """mmd_level_spmv_timed computes the same product as mmd_level_spmv (same
+    kernel, bit-identical) and reports a positive kernel time."""
+    A, D = fd_case
+    h = _handle(A, n_coarse=60)
+    x = np.random.default_rng(5).standard_normal(A.n)
+    y1 = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    y2 = torch.zeros_like(y1)
+    ms = h.level_spmv_timed(0, 0, _dev(x), y1, reps=3)
+    h.level_spmv(0, 0, _dev(x), y2)
+    assert ms > 0
+    assert torch.equal(y1, y2)
+    ref = A.to_scipy() @ x
+    assert np.abs(y1.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    h.close()
+
+
 @pytest.mark.parametrize("k", [0, 1, 2])
 def test_level_op_matches_oracle(fd_case, k):
     A, D = fd_case
