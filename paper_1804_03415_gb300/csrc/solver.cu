@@ -18,7 +18,7 @@
 //
 // Precision: T = double (every step FP64) or T = float (matrix values,
 // vectors and per-thread sums in FP32; block sums and scalars in FP64).  The
-// FP32 instance is the inner solver of the mixed mode, wrapped by the driver
+// FP32 instance is the inner solver of the mixed mode, wrapped in driver.cu
 // in FP64 iterative refinement (FP64 residual b - A x, FP32 correction).
 //
 // Modes
