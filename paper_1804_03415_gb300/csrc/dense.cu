@@ -8,16 +8,16 @@
 // classical sequential algorithms are restructured for parallel hardware:
 //   * tridiagonal eigenvalues: Sturm-sequence bisection, one thread per
 //     eigenvalue (Golub and Van Loan, Section 8.4);
-//   * tridiagonal eigenvectors: inverse iteration with a partially pivoted
-//     tridiagonal LU, one thread per cluster of close eigenvalues, modified
-//     Gram-Schmidt inside a cluster (Wilkinson's inverse iteration);
+//   * tridiagonal eigenvectors: implicit QL with Wilkinson shifts, the
+//     rotations applied to the rows of Z in parallel, or to the last row
+//     only when just the Ritz estimates are wanted;
 //   * p explicitly shifted QR steps, one Givens sweep each: the p sweeps
 //     move down the matrix together, sweep j three positions behind sweep
 //     j-1, so one step of the schedule performs up to p independent
 //     rotations; the rotations are recorded and applied to Q by many
 //     blocks, one row of Q per thread;
-//   * dense symmetric eigenproblems: Householder tridiagonalisation on one
-//     block, then the two tridiagonal kernels and a parallel back-transform.
+//   * dense symmetric eigenproblems (Rayleigh-Ritz S, coarsest pencil):
+//     cooperative two-sided Jacobi, round-robin pairs across blocks.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -90,113 +90,6 @@ __global__ void tri_bisect_kernel(const double* d, const double* e2, int n, cons
       lo = mid;
   }
   w[i] = 0.5 * (lo + hi);
-}
-
-// ------------------------------------------------------------ inverse iteration
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-// Clusters: consecutive eigenvalues closer than ortol start a shared cluster.
-__global__ void tri_clusters_kernel(const double* w, int n, const double* bounds, int* cstart, int* ncl) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double nrm = fmax(fabs(bounds[0]), fabs(bounds[1]));
-  const double ortol = 1e-3 * nrm;
-  int c = 0;
-  cstart[c++] = 0;
-  for (int i = 1; i < n; ++i)
-    if (w[i] - w[i - 1] > ortol) cstart[c++] = i;
-  cstart[c] = n;
-  *ncl = c;
-}
-
-// One thread per cluster; work: 5n doubles per thread (D, DU, DU2, DL, x) + n ints
-__global__ void tri_inviter_kernel(const double* d, const double* e, int n, const double* w, const int* cstart,
-                                   const int* ncl, const double* bounds, double* Z, int ldz, double* work,
-                                   int* iwork) {
-  const int cl = blockIdx.x * blockDim.x + threadIdx.x;
-  if (cl >= *ncl) return;
-  const double nrm = fmax(fmax(fabs(bounds[0]), fabs(bounds[1])), 1e-300);
-  const double tiny = kEps * nrm;
-  double* D = work + size_t(cl) * 5 * n;
-  double* DU = D + n;
-  double* DU2 = DU + n;
-  double* DL = DU2 + n;
-  double* x = DL + n;
-  int* piv = iwork + size_t(cl) * n;
-  const int i0 = cstart[cl], i1 = cstart[cl + 1];
-  for (int i = i0; i < i1; ++i) {
-    // perturb members of a cluster apart so the factorisations differ
-    const double lam = w[i] + (i - i0) * 10 * kEps * nrm;
-    for (int k = 0; k < n; ++k) {
-      D[k] = d[k] - lam;
-      if (k < n - 1) {
-        DU[k] = e[k];
-        DL[k] = e[k];
-      }
-      DU2[k] = 0;
-    }
-    for (int k = 0; k < n - 1; ++k) {
-      if (fabs(D[k]) >= fabs(DL[k])) {
-        if (D[k] == 0.0) D[k] = tiny;
-        const double l = DL[k] / D[k];
-        DL[k] = l;
-        D[k + 1] -= l * DU[k];
-        piv[k] = 0;
-      } else {
-        const double l = D[k] / DL[k];
-        D[k] = DL[k];
-        DL[k] = l;
-        const double t = DU[k];
-        DU[k] = D[k + 1];
-        D[k + 1] = t - l * D[k + 1];
-        if (k < n - 2) {
-          DU2[k] = DU[k + 1];
-          DU[k + 1] = -l * DU[k + 1];
-        }
-        piv[k] = 1;
-      }
-    }
-    if (D[n - 1] == 0.0) D[n - 1] = tiny;
-    for (int k = 0; k < n; ++k) x[k] = 1.0 + 0.5 * ((double)(mix64(uint64_t(i) * 1000003ull + k) >> 11) * 0x1.0p-53 - 0.5);
-    for (int itr = 0; itr < 3; ++itr) {
-      // solve (L U) y = x with the recorded row interchanges
-      for (int k = 0; k < n - 1; ++k) {
-        if (piv[k]) {
-          const double t = x[k];
-          x[k] = x[k + 1];
-          x[k + 1] = t;
-        }
-        x[k + 1] -= DL[k] * x[k];
-      }
-      x[n - 1] /= D[n - 1];
-      if (n > 1) x[n - 2] = (x[n - 2] - DU[n - 2] * x[n - 1]) / D[n - 2];
-      for (int k = n - 3; k >= 0; --k) x[k] = (x[k] - DU[k] * x[k + 1] - DU2[k] * x[k + 2]) / D[k];
-      // orthogonalise against earlier members of the cluster (MGS), normalise
-      for (int j = i0; j < i; ++j) {
-        const double* zj = Z + size_t(j) * ldz;
-        double s = 0;
-        for (int k = 0; k < n; ++k) s = fma(zj[k], x[k], s);
-        for (int k = 0; k < n; ++k) x[k] = fma(-s, zj[k], x[k]);
-      }
-      double nr = 0, mx = 0;
-      for (int k = 0; k < n; ++k) mx = fmax(mx, fabs(x[k]));
-      if (mx == 0.0) {
-        x[(i - i0) % n] = 1.0;
-        mx = 1.0;
-      }
-      for (int k = 0; k < n; ++k) {
-        x[k] /= mx;
-        nr = fma(x[k], x[k], nr);
-      }
-      nr = 1.0 / sqrt(nr);
-      for (int k = 0; k < n; ++k) x[k] *= nr;
-    }
-    double* zi = Z + size_t(i) * ldz;
-    for (int k = 0; k < n; ++k) zi[k] = x[k];
-  }
 }
 
 // ------------------------------------------------------------ QR sweeps
@@ -532,98 +425,6 @@ __global__ void permute_cols_kernel(const double* A, int lda, int64_t nrows, con
   }
 }
 
-// ------------------------------------------------------------ dense symmetric
-// Householder tridiagonalisation of A (n x n, lower part used), one block.
-// On exit: d, e; reflector k stored in column k of V (entries k+1..n-1) with tau[k].
-__global__ void sytrd_kernel(double* A, int lda, int n, double* d, double* e, double* tau, double* wv) {
-  __shared__ double red[32];
-  __shared__ double s_alpha, s_tau, s_scale;
-  double* v = wv;       // n
-  double* w = wv + n;   // n
-  for (int k = 0; k < n - 2; ++k) {
-    // x = A[k+1:, k]
-    double ss = 0;
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) ss = fma(A[i + size_t(k) * lda], A[i + size_t(k) * lda], ss);
-    ss = block_sum(ss, red);
-    if (threadIdx.x == 0) {
-      const double x0 = A[k + 1 + size_t(k) * lda];
-      const double nx = sqrt(ss);
-      if (nx == 0.0) {
-        s_tau = 0.0;
-        s_alpha = x0;
-        s_scale = 0.0;
-      } else {
-        const double alpha = x0 >= 0 ? -nx : nx;  // new subdiagonal
-        const double v0 = x0 - alpha;
-        s_alpha = alpha;
-        s_tau = -v0 / alpha;         // H = I - tau v v^T, v[0] = 1
-        s_scale = 1.0 / v0;
-      }
-    }
-    __syncthreads();
-    const double tk = s_tau;
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x)
-      v[i] = (i == k + 1) ? 1.0 : A[i + size_t(k) * lda] * s_scale;
-    __syncthreads();
-    if (tk != 0.0) {
-      // w = tau * A22 v  (A22 = A[k+1:, k+1:], symmetric, use lower triangle)
-      for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
-        double s = 0;
-        for (int j = k + 1; j < n; ++j) {
-          const double aij = (i >= j) ? A[i + size_t(j) * lda] : A[j + size_t(i) * lda];
-          s = fma(aij, v[j], s);
-        }
-        w[i] = tk * s;
-      }
-      __syncthreads();
-      double vw = 0;
-      for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) vw = fma(v[i], w[i], vw);
-      vw = block_sum(vw, red);
-      const double K = -0.5 * tk * vw;
-      for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) w[i] = fma(K, v[i], w[i]);
-      __syncthreads();
-      // A22 -= v w^T + w v^T (lower triangle)
-      for (int j = k + 1; j < n; ++j)
-        for (int i = j + threadIdx.x; i < n; i += blockDim.x)
-          A[i + size_t(j) * lda] -= v[i] * w[j] + w[i] * v[j];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      d[k] = A[k + size_t(k) * lda];
-      e[k] = s_alpha;
-      tau[k] = tk;
-    }
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + size_t(k) * lda] = v[i];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    if (n >= 2) {
-      d[n - 2] = A[n - 2 + size_t(n - 2) * lda];
-      e[n - 2] = A[n - 1 + size_t(n - 2) * lda];
-      tau[n - 2] = 0.0;
-    }
-    d[n - 1] = A[n - 1 + size_t(n - 1) * lda];
-  }
-}
-
-// Z <- H_0 H_1 ... H_{n-3} Z, one column of Z per thread group (warp).
-__global__ void ormtr_kernel(const double* A, int lda, int n, const double* tau, double* Z, int ldz, int ncol) {
-  const int lane = threadIdx.x & 31;
-  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (col >= ncol) return;
-  double* z = Z + size_t(col) * ldz;
-  for (int k = n - 3; k >= 0; --k) {
-    const double t = tau[k];
-    if (t == 0.0) continue;
-    // v = [1, A[k+2:, k]] on rows k+1..n-1
-    double s = 0;
-    for (int i = k + 1 + lane; i < n; i += 32) s = fma((i == k + 1) ? 1.0 : A[i + size_t(k) * lda], z[i], s);
-    s = warp_sum(s) * t;
-    for (int i = k + 1 + lane; i < n; i += 32) z[i] = fma(-s, (i == k + 1) ? 1.0 : A[i + size_t(k) * lda], z[i]);
-    __syncwarp();
-  }
-}
-
 // ------------------------------------------------------------ Cholesky family
 __global__ void potrf_upper_kernel(double* A, int lda, int n, int* status) {
   // A = R^T R, R upper stored in the upper triangle; one block, right-looking
@@ -785,15 +586,6 @@ void k_tri_eigvals(const double* d, const double* e, int n, double* w, cudaStrea
   tri_bisect_kernel<<<(n + 63) / 64, 64, 0, st>>>(d, g_tri.e2, n, g_tri.bounds, w);
 }
 
-void k_tri_eigvecs(const double* d, const double* e, int n, const double* w, double* Z, int ldz, double* work,
-                   cudaStream_t st) {
-  (void)work;
-  tri_bounds_kernel<<<1, 256, 0, st>>>(d, e, n, g_tri.bounds, g_tri.e2);
-  tri_clusters_kernel<<<1, 32, 0, st>>>(w, n, g_tri.bounds, g_tri.cstart, g_tri.ncl);
-  tri_inviter_kernel<<<(n + 31) / 32, 32, 0, st>>>(d, e, n, w, g_tri.cstart, g_tri.ncl, g_tri.bounds, Z, ldz,
-                                                   g_tri.work, g_tri.iwork);
-}
-
 void k_tri_ql(const double* d, const double* e, int n, double* w, double* Z, int ldz, double* zl, int* status,
               cudaStream_t st) {
   static std::once_flag attr_once;
@@ -815,26 +607,6 @@ void k_tri_qr_sweeps(double* d, double* e, int n, const double* sh, int p, doubl
   });
   tri_chase_kernel<<<1, 512, smem, st>>>(d, e, n, sh, p, rc, rs, nsteps);
   tri_apply_rot_kernel<<<(n + 7) / 8, 8, 0, st>>>(n, p, nsteps, rc, rs, Q, ldq);
-}
-
-int k_syev(double* A, int lda, int n, double* w, double* Z, int ldz, double* work, int* dev_status,
-           cudaStream_t st) {
-  (void)dev_status;
-  // work: d (n), e (n), tau (n), wv (2n)
-  double* d = work;
-  double* e = d + n;
-  double* tau = e + n;
-  double* wv = tau + n;
-  if (n == 1) {
-    cudaMemcpyAsync(w, A, sizeof(double), cudaMemcpyDeviceToDevice, st);
-    identity_kernel<<<1, 32, 0, st>>>(Z, ldz, 1);
-    return 0;
-  }
-  sytrd_kernel<<<1, 1024, 0, st>>>(A, lda, n, d, e, tau, wv);
-  k_tri_eigvals(d, e, n, w, st);
-  k_tri_eigvecs(d, e, n, w, Z, ldz, nullptr, st);
-  ormtr_kernel<<<(n * 32 + 255) / 256, 256, 0, st>>>(A, lda, n, tau, Z, ldz, n);
-  return 0;
 }
 
 static thread_local int g_coop_cap = 0;

@@ -105,19 +105,13 @@ void k_residuals(const Sell& A, int64_t n, const double* V, int64_t ld, int m, c
 // ---- small dense (dense.cu); all matrices column-major
 // eigenvalues of symmetric tridiagonal (d: n, e: n-1) by bisection, ascending
 void k_tri_eigvals(const double* d, const double* e, int n, double* w, cudaStream_t st);
-// eigenvectors of symmetric tridiagonal for eigenvalues w (ascending), Z: n x n (ldz)
-void k_tri_eigvecs(const double* d, const double* e, int n, const double* w, double* Z, int ldz, double* work,
-                   cudaStream_t st);
 // implicit-QR eigen-decomposition of a symmetric tridiagonal (n <= 6000):
 // w ascending; Z (n x n) full eigenvectors if non-NULL; zl (n) last row of Z if non-NULL
 void k_tri_ql(const double* d, const double* e, int n, double* w, double* Z, int ldz, double* zl, int* status,
               cudaStream_t st);
-// p shifted implicit QR sweeps on tridiagonal (d, e) of order n with shifts sh[0..p-1];
+// p explicitly shifted QR steps on tridiagonal (d, e) of order n with shifts sh[0..p-1];
 // Q (n x n) is overwritten with the accumulated orthogonal factor (starting from I).
 void k_tri_qr_sweeps(double* d, double* e, int n, const double* sh, int p, double* Q, int ldq, cudaStream_t st);
-// dense symmetric eig: A (n x n) -> w ascending, Z eigenvectors (may alias A). work: >= 4 n^2 + 8 n doubles
-int k_syev(double* A, int lda, int n, double* w, double* Z, int ldz, double* work, int* dev_status,
-           cudaStream_t st);
 // parallel two-sided Jacobi (cooperative): S (m x m, ld m) -> diagonal (eigenvalues, unsorted),
 // V (m x m) eigenvectors; work >= m + 4 doubles, iwork >= 30 ints
 cudaError_t k_syev_jacobi(double* S, int m, double* V, double* work, int* iwork, GridBarrier bar, cudaStream_t st);
