@@ -30,11 +30,6 @@ __global__ void scal_kernel(double* x, int64_t n, double a) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     x[i] *= a;
 }
-__global__ void scal_dev_kernel(double* x, int64_t n, const double* a, int inv) {
-  const double s = inv ? 1.0 / a[0] : a[0];
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    x[i] *= s;
-}
 __global__ void axpy_kernel(double* y, const double* x, int64_t n, double a) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     y[i] = fma(a, x[i], y[i]);
@@ -387,9 +382,6 @@ void k_copy(double* y, const double* x, int64_t n, cudaStream_t st) {
   copy_kernel<<<nblk(n, 256), 256, 0, st>>>(y, x, n);
 }
 void k_scal(double* x, int64_t n, double a, cudaStream_t st) { scal_kernel<<<nblk(n, 256), 256, 0, st>>>(x, n, a); }
-void k_scal_dev(double* x, int64_t n, const double* a, int inv, cudaStream_t st) {
-  scal_dev_kernel<<<nblk(n, 256), 256, 0, st>>>(x, n, a, inv);
-}
 void k_axpy(double* y, const double* x, int64_t n, double a, cudaStream_t st) {
   axpy_kernel<<<nblk(n, 256), 256, 0, st>>>(y, x, n, a);
 }

@@ -549,14 +549,6 @@ __global__ void csr_dense_kernel(const int32_t* rp, const int32_t* ci, const dou
   for (int k = 0; k < n; ++k) D[i + size_t(k) * ldd] = 0.0;
   for (int32_t k = rp[i]; k < rp[i + 1]; ++k) D[i + size_t(ci[k]) * ldd] = va[k];
 }
-__global__ void identity_kernel(double* Q, int ldq, int n) {
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < int64_t(n) * n;
-       t += int64_t(gridDim.x) * blockDim.x) {
-    const int i = int(t % n), j = int(t / n);
-    Q[i + size_t(j) * ldq] = (i == j) ? 1.0 : 0.0;
-  }
-}
-
 inline int g1(int64_t n, int t) {
   int64_t b = (n + t - 1) / t;
   if (b > 4096) b = 4096;
@@ -675,8 +667,4 @@ void k_csr_to_dense(const int32_t* rp, const int32_t* ci, const double* va, int 
                     cudaStream_t st) {
   csr_dense_kernel<<<(n + 127) / 128, 128, 0, st>>>(rp, ci, va, n, D, ldd);
 }
-void k_set_identity(double* Q, int ldq, int n, cudaStream_t st) {
-  identity_kernel<<<g1(int64_t(n) * n, 256), 256, 0, st>>>(Q, ldq, n);
-}
-
 }  // namespace mmd

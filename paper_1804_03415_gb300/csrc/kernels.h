@@ -57,7 +57,6 @@ cudaError_t launch_solver(const SolverArgs& a, int mt, int grid, cudaStream_t st
 void k_fill(double* x, int64_t n, double v, cudaStream_t st);
 void k_copy(double* y, const double* x, int64_t n, cudaStream_t st);
 void k_scal(double* x, int64_t n, double a, cudaStream_t st);
-void k_scal_dev(double* x, int64_t n, const double* a, int invert, cudaStream_t st);
 void k_axpy(double* y, const double* x, int64_t n, double a, cudaStream_t st);
 // y = A x (SELL-32), columns m of ld (x, y column-major)
 void k_spmv(const Sell& A, const double* x, int64_t ldx, double* y, int64_t ldy, int m, cudaStream_t st);
@@ -135,7 +134,4 @@ void k_transpose_sq(const double* A, int lda, int n, double* B, int ldb, cudaStr
 void k_symmetrise(double* A, int lda, int n, cudaStream_t st);
 void k_csr_to_dense(const int32_t* rp, const int32_t* ci, const double* va, int n, double* D, int ldd,
                     cudaStream_t st);
-// tridiagonal (alpha, beta) -> dense-free utilities
-void k_set_identity(double* Q, int ldq, int n, cudaStream_t st);
-
 }  // namespace mmd
