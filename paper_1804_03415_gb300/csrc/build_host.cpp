@@ -86,17 +86,32 @@ void jacobi_eig(int n, std::vector<double>& a, std::vector<double>& w, std::vect
 
 // In-place lower Cholesky of an n x n row-major SPD matrix.  Returns false if
 // a pivot is not positive.
+// sum_{k < len} x[k] y[k] with four independent partial sums (the row dot
+// products of the Cholesky below are its whole cost; one accumulator would
+// serialise on the FMA latency)
+static inline double dot4(const double* x, const double* y, int len) {
+  double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  int k = 0;
+  for (; k + 4 <= len; k += 4) {
+    s0 += x[k] * y[k];
+    s1 += x[k + 1] * y[k + 1];
+    s2 += x[k + 2] * y[k + 2];
+    s3 += x[k + 3] * y[k + 3];
+  }
+  for (; k < len; ++k) s0 += x[k] * y[k];
+  return (s0 + s1) + (s2 + s3);
+}
+
 bool cholesky(int n, std::vector<double>& a) {
   for (int j = 0; j < n; ++j) {
-    double s = a[size_t(j) * n + j];
-    for (int k = 0; k < j; ++k) s -= a[size_t(j) * n + k] * a[size_t(j) * n + k];
+    const double* aj = a.data() + size_t(j) * n;
+    const double s = a[size_t(j) * n + j] - dot4(aj, aj, j);
     if (!(s > 0)) return false;
-    double d = std::sqrt(s);
+    const double d = std::sqrt(s);
     a[size_t(j) * n + j] = d;
     for (int i = j + 1; i < n; ++i) {
-      double t = a[size_t(i) * n + j];
-      for (int k = 0; k < j; ++k) t -= a[size_t(i) * n + k] * a[size_t(j) * n + k];
-      a[size_t(i) * n + j] = t / d;
+      double* ai = a.data() + size_t(i) * n;
+      ai[j] = (ai[j] - dot4(ai, aj, j)) / d;
     }
   }
   return true;
@@ -514,7 +529,26 @@ bool localized_psi(const HCSR& A, const std::vector<int32_t>& patch_of, const st
     }
     std::vector<double> Cx(size_t(nc) * m);
     Cx = Y;  // C rows (phi restricted), kept for S = C Y
-    for (int ai = 0; ai < nc; ++ai) chol_solve(m, L, Y.data() + size_t(ai) * m);
+    // L L^T y = c for every constraint row; the backward sweep reads L^T by
+    // rows (same sums, same order as chol_solve, contiguous loads)
+    std::vector<double> LT(size_t(m) * m);
+    for (int x = 0; x < m; ++x)
+      for (int y = 0; y <= x; ++y) LT[size_t(y) * m + x] = L[size_t(x) * m + y];
+    for (int ai = 0; ai < nc; ++ai) {
+      double* b = Y.data() + size_t(ai) * m;
+      for (int i = 0; i < m; ++i) {
+        double t = b[i];
+        const double* Li = L.data() + size_t(i) * m;
+        for (int k = 0; k < i; ++k) t -= Li[k] * b[k];
+        b[i] = t / Li[i];
+      }
+      for (int i = m - 1; i >= 0; --i) {
+        double t = b[i];
+        const double* Ui = LT.data() + size_t(i) * m;
+        for (int k = i + 1; k < m; ++k) t -= Ui[k] * b[k];
+        b[i] = t / Ui[i];
+      }
+    }
     std::vector<double> S(size_t(nc) * nc, 0.0);
     for (int ai = 0; ai < nc; ++ai)
       for (int bi = 0; bi < nc; ++bi) {
