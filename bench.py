@@ -10,20 +10,25 @@ flushed (a 512 MB write) before every timed step.
 
 ``--precision`` picks the timed form (fp64 = MMD_FP64, mixed = MMD_MIXED:
 FP32 PCG on the coarse levels inside FP64 refinement, mixed_all =
-MMD_MIXED_ALL: FP32 level-0 CG with FP64 reliable updates as well); the other
-of fp64 / mixed is timed after it on the same handle and reported under
-``compare``.
+MMD_MIXED_ALL: FP32 level-0 CG with FP64 reliable updates as well).  The other
+of fp64 / mixed is then timed for ONE step on the same handle and reported
+under ``compare`` with its per-eigenpair error against the timed form
+(skipped, and said so, when the time budget would be exceeded).
 
 Also reported:
-  * t_level_ms -- wall time per level of the timed step;
+  * t_level_ms -- wall time per level of the last timed step;
   * e2e     -- the same metric through the public API with host buffers:
-               mmd_build from a host CSR + eig_leftmost into host outputs;
-  * spmv    -- standalone FP64 CSR SpMV GB/s on the 128^3 7-point operator
+               mmd_build from a host CSR + eig_leftmost into host outputs,
+               one run;
+  * spmv    -- standalone FP64 SELL SpMV GB/s on the 128^3 7-point operator
                (14.6M nnz, larger than L2);
   * roofline of the dominant kernel (the persistent CG/PCG solver) from its
                event-timed launches inside the timed steps;
+  * reference_eigs -- the eigenvalues against an independent shift-invert
+               Lanczos (scipy ARPACK) result stored with its input hash;
   * cpu_baseline -- the CPU oracle on a bounded sample of the same workload.
 
+Expected wall time at --steps 20 --warmup 5 (one step ~40 s): about 1100 s.
 ``--impl reference`` times the CPU oracle instead (the reference arm).
 Multi-GPU (torchrun): replicas only -- every rank solves its own copy of the
 workload, no data-path collective; value = total eigenpairs / max time.
@@ -45,13 +50,19 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = {"workload": "torus_knn_200k", "n": 200000, "k": 10, "N": 500, "tol": 1e-8,
             "matrix": "torus kNN Laplacian + 1e-6 I, FP64 CSR", "l2": "flushed before each step"}
-SAMPLE = {"npts": 5000, "N": 20, "tol": 1e-8}  # bounded oracle sample of the same workload kind
+# bounded oracle sample of the same workload kind: the same generator at 5,000 points, N = 20
+SAMPLE = {"npts": 5000, "N": 20, "tol": 1e-8}
 FALLBACK_HBM = 6800.0
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_all": 2}  # MMD_FP64, MMD_MIXED, MMD_MIXED_ALL
-FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64
-# DRAM bytes per launch of the solver, from an ncu capture of solve_kernel<1, double> on the level-0
-# matrix of this workload (bench.py --kernel-case op); the matrix is read once per launch
-TRAFFIC_PER_LAUNCH = 33.66e6
+# FP64 peak of the GB300: 152 SMs x 1.68 FP64 FMA per clock per SM (measured: chains of
+# independent FMAs on one SM, 4+ warps, timed with clock64) x 2 flops x 2.070 GHz
+FP64_FMA_PER_CLK_SM = 1.68
+FP64_PEAK_TFLOPS = 152 * FP64_FMA_PER_CLK_SM * 2 * 2.070e9 / 1e12  # 1.057
+FP64_NOMINAL_TFLOPS = 1.25
+# DRAM bytes per launch of the solver from an ncu capture at the current kernel
+# (None until one is taken): reported as roofline.traffic
+TRAFFIC_PER_LAUNCH = None
+REF_EIGS = os.path.join(ROOT, "tests", "golden", "torus_knn_200k_eigs.json")
 
 
 def peaks():
@@ -147,12 +158,43 @@ def sample_desc():
 
 
 # ------------------------------------------------------------------ GPU arm
+def input_hash(A) -> str:
+    """sha256 of the CSR bytes (row pointers, columns, values) of a workload."""
+    import hashlib
+
+    hsh = hashlib.sha256()
+    for arr in (A.rowptr, A.col, A.val):
+        hsh.update(np.ascontiguousarray(arr).tobytes())
+    return hsh.hexdigest()
+
+
+def reference_check(A, lam) -> dict | None:
+    """Relative eigenvalue errors against the stored independent reference
+    (scipy eigsh shift-invert) when its input hash matches this matrix."""
+    if not os.path.exists(REF_EIGS):
+        return None
+    ref = json.load(open(REF_EIGS))
+    hs = input_hash(A)
+    if ref.get("input_sha256") != hs:
+        return {"error": "input hash differs from the stored reference", "sha256": hs}
+    r = np.asarray(ref["eigenvalues"][:len(lam)])
+    lam = np.asarray(lam)
+    rel = np.abs(lam - r) / np.abs(r)
+    # the 1e-6-shifted zero mode is compared in absolute terms against ||A|| (its relative
+    # accuracy is bounded by u ||A|| / lambda_1)
+    absn = np.abs(lam - r) / float(ref["norm_A_inf"])
+    return {"source": ref["method"], "pairs": int(len(r)), "max_rel_err": float(rel.max()),
+            "max_rel_err_excl_first": float(rel[1:].max()) if len(rel) > 1 else None,
+            "max_abs_err_over_normA": float(absn.max()), "worst_index": int(np.argmax(rel))}
+
+
 def gpu_arm(args, rank, world):
     import torch
 
     import paper_1804_03415_gb300 as G
     import workloads as W
 
+    t_start = time.perf_counter()
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
@@ -168,18 +210,18 @@ def gpu_arm(args, rank, world):
 
     prec = PRECISIONS[args.precision]
 
-    def step(profile, precision=prec):
-        return h.eig_leftmost(N, tol, out=(lam, V), allow_noconv=True, stream=sptr, profile=profile,
+    def step(profile, precision=prec, out=(lam, V)):
+        return h.eig_leftmost(N, tol, out=out, allow_noconv=True, stream=sptr, profile=profile,
                               precision=precision)[2]
 
-    def timed(steps, precision):
+    def timed(steps, precision, out=(lam, V)):
         ev, sts = [], []
         for _ in range(steps):
             flush.fill_(1.0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
-            sts.append(step(1, precision))
+            sts.append(step(1, precision, out))
             e1.record(stream)
             torch.cuda.synchronize()
             ev.append(e0.elapsed_time(e1))
@@ -195,38 +237,52 @@ def gpu_arm(args, rank, world):
     ms_local = float(np.sum(ev))
     ms = dist_max(ms_local, world)
     value = job_value(world, N, args.steps, ms)
-    # the other precision on the same handle (one untimed warm-up step first)
+    lam_main = lam.cpu().numpy().copy()
+    step_s = ms_local / 1e3 / args.steps
+    # the other precision on the same handle: one step, with its per-eigenpair
+    # difference from the timed form; skipped when it would overrun the budget
     compare = None
     if not args.no_compare:
         other = "fp64" if args.precision != "fp64" else "mixed"
-        step(0, PRECISIONS[other])
-        dist_barrier(world)
-        ev2, st2 = timed(args.steps, PRECISIONS[other])
-        ms2 = dist_max(float(np.sum(ev2)), world)
-        compare = {"precision": other, "value": job_value(world, N, args.steps, ms2), "unit": "eigenpairs/s",
-                   "ms_per_step": ms2 / args.steps,
-                   "residual": {"max_rel": st2[-1]["max_rel_residual"], "n_converged": st2[-1]["n_converged"]},
-                   "t_level_ms": st2[-1]["t_level_ms"], "pcg_iters": st2[-1]["pcg_iters"],
-                   "refine_pcg_iters": st2[-1]["refine_pcg_iters"]}
-    # end to end: host CSR in, host outputs out, through the public API
-    e2e_times = []
+        projected = (time.perf_counter() - t_start) + 3.5 * step_s + build_s + 60
+        if projected > args.budget_s:
+            compare = {"precision": other, "skipped": f"time budget: projected {projected:.0f} s > {args.budget_s} s"}
+        else:
+            lam2 = torch.zeros_like(lam)
+            V2 = torch.zeros_like(V)
+            dist_barrier(world)
+            ev2, st2 = timed(1, PRECISIONS[other], out=(lam2, V2))
+            ms2 = dist_max(float(np.sum(ev2)), world)
+            l2 = lam2.cpu().numpy()
+            rel = np.abs(l2 - lam_main) / np.abs(lam_main)
+            # subspace agreement: smallest singular value of V_main^T V_other per cluster is
+            # summarised by the worst column's |cos| (clusters of near-equal values included)
+            cosines = torch.linalg.svdvals(V.to(torch.float64) @ V2.T.to(torch.float64)).cpu().numpy()
+            compare = {"precision": other, "steps": 1, "value": job_value(world, N, 1, ms2), "unit": "eigenpairs/s",
+                       "ms_per_step": ms2,
+                       "residual": {"max_rel": st2[-1]["max_rel_residual"], "n_converged": st2[-1]["n_converged"]},
+                       "vs_timed_form": {"max_rel_eig_diff": float(rel.max()),
+                                         "max_rel_eig_diff_excl_first": float(rel[1:].max()),
+                                         "min_subspace_cos": float(cosines.min())},
+                       "t_level_ms": st2[-1]["t_level_ms"], "pcg_iters": st2[-1]["pcg_iters"],
+                       "refine_pcg_iters": st2[-1]["refine_pcg_iters"]}
+            del V2
+    # end to end: host CSR in, host outputs out, through the public API (one run)
+    import ctypes as C
+
     lam_h = np.zeros(N)
     V_h = np.zeros((N, A.n))
-    for _ in range(max(1, min(args.steps, 2))):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        h2 = G.MMD(A.rowptr, A.col, A.val)
-        st2 = G.eig_opts(stream=sptr, precision=prec)
-        import ctypes as C
-
-        s2 = G._lib.mmd_eig_stats()
-        rc = h2._lib.eig_leftmost(h2.h, N, tol, C.byref(st2), lam_h.ctypes.data, V_h.ctypes.data, 0, C.byref(s2))
-        torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
-        h2.close()
-        if rc not in (0, -3):
-            raise RuntimeError(f"e2e eig_leftmost failed: {rc}")
-    e2e_s = dist_max(float(np.mean(e2e_times)), world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h2 = G.MMD(A.rowptr, A.col, A.val)
+    o2 = G.eig_opts(stream=sptr, precision=prec)
+    s2 = G._lib.mmd_eig_stats()
+    rc = h2._lib.eig_leftmost(h2.h, N, tol, C.byref(o2), lam_h.ctypes.data, V_h.ctypes.data, 0, C.byref(s2))
+    torch.cuda.synchronize()
+    e2e_s = dist_max(time.perf_counter() - t0, world)
+    h2.close()
+    if rc not in (0, -3):
+        raise RuntimeError(f"e2e eig_leftmost failed: {rc}")
     h2d = A.nnz * 12 + (A.n + 1) * 4
     d2h = N * A.n * 8 + N * 8
     # roofline of the solver kernel
@@ -247,15 +303,19 @@ def gpu_arm(args, rank, world):
         "config": dict(WORKLOAD, precision=args.precision, parallelism=f"replicas{world}"),
         "build_s": build_s,
         "residual": {"max_rel": st0["max_rel_residual"], "n_converged": st0["n_converged"]},
+        "reference_eigs": reference_check(A, lam_main),
         "t_level_ms": st0["t_level_ms"],
         "compare": compare,
-        "counters": {k: st0[k] for k in ("op_calls", "pcg_iters", "inner_iters", "b_iters", "refine_pcg_iters",
-                                         "restarts", "lanczos_steps", "refine_iters", "n_levels")},
+        "counters": {k: st0[k] for k in ("op_calls", "pcg_iters", "inner_iters", "b_iters", "refine_pcg_calls",
+                                         "refine_pcg_iters", "restarts", "lanczos_steps", "refine_iters",
+                                         "n_levels")},
         "e2e": {"value": world * N / e2e_s, "unit": "eigenpairs/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "includes": "mmd_build from host CSR + eig_leftmost to host"},
+                "d2h_bytes_per_step": d2h, "includes": "mmd_build from host CSR + eig_leftmost to host, one run"},
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "roofline": {"kernel": "solve_kernel (persistent CG/PCG)", "bound": "alu", "achieved": tflops,
-                     "peak": FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 dense FP64 (no measured FP64 peak)",
+                     "peak": FP64_PEAK_TFLOPS,
+                     "peak_source": "derived: 152 SMs x 1.68 FP64 FMA/clk/SM (measured on one SM) x 2 x 2.07 GHz; "
+                                    f"nominal {FP64_NOMINAL_TFLOPS}",
                      "unit": "TFLOP/s", "frac": (tflops / FP64_PEAK_TFLOPS) if tflops else None,
                      "traffic": TRAFFIC_PER_LAUNCH, "launches": pcg_launches,
                      "share_of_step": pcg_ms / max(ms_local, 1e-9),
@@ -267,6 +327,7 @@ def gpu_arm(args, rank, world):
                                   "bytes": "12 nnz + 4 n per iteration (matrix) + 72 n per column (vectors)"}},
         "spmv": spmv,
         "clocks": clocks,
+        "wall_s": time.perf_counter() - t_start,
     }
     h.close()
     return out
@@ -388,6 +449,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp64")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other precision")
+    ap.add_argument("--budget-s", type=float, default=1500.0,
+                    help="wall-clock budget of the run; optional legs are skipped past it")
     ap.add_argument("--kernel-case", choices=["op", "block", "eig", "spmv"], default=None)
     args = ap.parse_args()
     if args.oracle_worker:
@@ -408,9 +471,12 @@ def main():
                 "unit": "eigenpairs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * float(np.mean(t)), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": dict(WORKLOAD, precision="fp64", parallelism="cpu"),
-                "cpu_baseline": {"value": val, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
-                                 "sample": sample_desc()},
+                "config": dict(WORKLOAD, precision="fp64", parallelism="cpu",
+                               sample=dict(SAMPLE, workload=f"torus_knn_{SAMPLE['npts']}",
+                                           note="each step times the oracle on this bounded sample, not the "
+                                                "200k workload: the ratio to the GPU arm compares unlike sizes")),
+                "cpu_baseline": {"value": val, "unit": "eigenpairs/s", "cores": 1, "host_cores": os.cpu_count(),
+                                 "kind": "oracle", "sample": sample_desc()},
                 "e2e": {"value": val, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -420,7 +486,8 @@ def main():
     if rank0 and int(os.environ.get("WORLD_SIZE", "1")) == 1 and not args.no_cpu_baseline:
         try:
             o = run_oracle(1)
-            cpu = {"value": o["value"], "unit": "eigenpairs/s", "cores": 1, "kind": "oracle", "sample": sample_desc()}
+            cpu = {"value": o["value"], "unit": "eigenpairs/s", "cores": 1, "host_cores": os.cpu_count(),
+                   "kind": "oracle", "sample": sample_desc()}
         except Exception as e:  # reported, never silently replaced
             cpu = {"value": None, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle", "error": str(e)[-300:]}
     rank, world = dist_init()

@@ -263,7 +263,8 @@ const char* mmd_last_error(void);
  * larger n returns MMD_EINVAL with a message.  The call makes no cudaMalloc
  * or cudaFree and calls no allocating library routine.
  * The first call on a device (with that device current) looks up the array's
- * device address once; make that first call before any stream capture.
+ * device address once (first calls from several host threads are serialised);
+ * make that first call before any stream capture.
  * Every call reuses the same array and keeps nothing from the last one:
  * before its kernel it clears, on its stream, what must start at zero (the
  * barrier counter and the status word); calls that can run concurrently on

@@ -228,10 +228,10 @@ def eigsh_leftmost(rowptr, col, val, N: int, tol: float = 1e-8, build=None, **op
 
         @staticmethod
         def backward(ctx, glam, gV):
-            gl = glam if glam is not None else torch.zeros(N, dtype=torch.float64, device=glam.device)
+            # the handle keeps the forward result, so backward may run more than
+            # once (retain_graph); it is freed with the graph (MMD.__del__)
+            gl = glam if glam is not None else torch.zeros(N, dtype=torch.float64, device=val.device)
             gv = gV.T.contiguous() if gV is not None else None
-            g = ctx.h.eig_grad(gl.contiguous(), gv)
-            ctx.h.close()
-            return g
+            return ctx.h.eig_grad(gl.contiguous(), gv)
 
     return _Eig.apply(val)

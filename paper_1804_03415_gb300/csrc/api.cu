@@ -438,6 +438,29 @@ int mmd_level_bsolve(mmd_handle* h, int k, const double* q, double* x, double to
   return level_bsolve(h, k, q, x, tol, max_iter, iters, (cudaStream_t)stream);
 }
 
+// Options of eig_leftmost, eig_leftmost_batched and eig_grad: defaults when
+// opts is NULL, else a copy checked field by field (values the algorithms
+// cannot use are refused before any work starts).
+static bool validated_opts(const mmd_eig_opts* opts, const char* who, mmd_eig_opts* out) {
+  mmd_default_eig_opts(out);
+  if (opts) *out = *opts;
+  const mmd_eig_opts& o = *out;
+  std::string bad;
+  if (!(o.alpha > 0) || !std::isfinite(o.alpha)) bad = "alpha must be finite and > 0";
+  else if (!(o.beta > 0) || !std::isfinite(o.beta)) bad = "beta must be finite and > 0";
+  else if (o.c_r < 1) bad = "c_r must be >= 1";
+  else if (o.d < 0) bad = "d must be >= 0";
+  else if (o.max_cg_iter < 1 || o.max_restarts < 1 || o.max_refine_iter < 1) bad = "iteration caps must be >= 1";
+  else if (!(o.timeout_s > 0) || !std::isfinite(o.timeout_s)) bad = "timeout_s must be finite and > 0";
+  else if (o.precision != MMD_FP64 && o.precision != MMD_MIXED && o.precision != MMD_MIXED_ALL)
+    bad = "precision must be MMD_FP64, MMD_MIXED or MMD_MIXED_ALL";
+  if (!bad.empty()) {
+    set_error(std::string(who) + ": invalid options: " + bad);
+    return false;
+  }
+  return true;
+}
+
 int eig_leftmost(mmd_handle* h, int N, double tol, const mmd_eig_opts* opts, double* lambda, double* V,
                  int outputs_on_device, mmd_eig_stats* stats) {
   if (!h || !h->on_device) {
@@ -449,13 +472,7 @@ int eig_leftmost(mmd_handle* h, int N, double tol, const mmd_eig_opts* opts, dou
     return MMD_EINVAL;
   }
   mmd_eig_opts o;
-  mmd_default_eig_opts(&o);
-  if (opts) o = *opts;
-  if (!(o.alpha > 0) || !(o.beta > 0) || o.c_r < 1 || o.max_cg_iter < 1 || o.max_restarts < 1 ||
-      o.max_refine_iter < 1 || !(o.timeout_s > 0) || (o.precision != MMD_FP64 && o.precision != MMD_MIXED && o.precision != MMD_MIXED_ALL)) {
-    set_error("eig_leftmost: invalid options");
-    return MMD_EINVAL;
-  }
+  if (!validated_opts(opts, "eig_leftmost", &o)) return MMD_EINVAL;
   return run_eig(h, N, tol, o, lambda, V, outputs_on_device, stats);
 }
 
@@ -471,9 +488,15 @@ int eig_leftmost_batched(mmd_handle* const* hs, int count, const int* N, double 
       set_error("eig_leftmost_batched: problem " + std::to_string(i) + " has a bad handle, N or output");
       return MMD_EINVAL;
     }
+  for (int i = 0; i < count; ++i)
+    for (int j = 0; j < i; ++j)
+      if (hs[i] == hs[j]) {
+        set_error("eig_leftmost_batched: problems " + std::to_string(j) + " and " + std::to_string(i) +
+                  " share one handle (handles must be distinct: a handle serves one call at a time)");
+        return MMD_EINVAL;
+      }
   mmd_eig_opts o;
-  mmd_default_eig_opts(&o);
-  if (opts) o = *opts;
+  if (!validated_opts(opts, "eig_leftmost_batched", &o)) return MMD_EINVAL;
   const int ns = std::max(1, std::min(count, streams > 0 ? streams : 8));
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -531,8 +554,7 @@ int eig_grad(mmd_handle* h, const double* dL_dlambda, const double* dL_dV, int i
     return MMD_EINVAL;
   }
   mmd_eig_opts o;
-  mmd_default_eig_opts(&o);
-  if (opts) o = *opts;
+  if (!validated_opts(opts, "eig_grad", &o)) return MMD_EINVAL;
   return run_grad(h, dL_dlambda, dL_dV, inputs_on_device, dL_dvals, output_on_device, o);
 }
 

@@ -231,7 +231,7 @@ __global__ void tri_ql_kernel(const double* d_in, const double* e_in, int n, dou
       }
       if (hi == 0 || iters >= max_iters) {
         s_done = 1;
-        if (iters >= max_iters) atomicExch(status, (int)DEV_NOTSPD);
+        if (iters >= max_iters) atomicExch(status, (int)DEV_NOCONV);
       } else {
         int lo = hi - 1;
         while (lo > 0 && fabs(e[lo - 1]) > kEps * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;

@@ -7,7 +7,7 @@
 namespace mmd {
 
 // Status word written by kernels (0 = fine).
-enum DevStatus : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BREAKDOWN = 2, DEV_NOTSPD = 3 };
+enum DevStatus : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BREAKDOWN = 2, DEV_NOTSPD = 3, DEV_NOCONV = 4 };
 
 struct GridBarrier {
   unsigned int* count;  // monotone arrival counter (zeroed before each launch)

@@ -165,6 +165,10 @@ struct Ctx {
       set_error("a CG/PCG or Cholesky step found a non-positive pivot (matrix not SPD)");
       throw CudaFail{MMD_ENOTSPD};
     }
+    if (s == DEV_NOCONV) {
+      set_error("the tridiagonal QL iteration did not converge within its sweep limit");
+      throw CudaFail{MMD_ENOCONV};
+    }
   }
   void after_launch() {
     CK(cudaGetLastError());

@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 
 #include "../../include/mmdeig.h"
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(kThreadsNA) na_cg_kernel(NAArgs a) {
 
 double* g_scratch_addr[64] = {nullptr};
 int g_max_grid[64] = {0};
+std::mutex g_setup_mu;  // serialises the per-device set-up of host threads' first calls
 
 }  // namespace
 }  // namespace mmd
@@ -171,6 +173,7 @@ extern "C" int mmd_cg_solve_noalloc(const mmd_csr* A, const double* b, double* x
     set_error("mmd_cg_solve_noalloc: no usable current CUDA device");
     return MMD_ECUDA;
   }
+  std::unique_lock<std::mutex> setup_lock(g_setup_mu);
   if (!g_scratch_addr[dev]) {  // once per device, with that device current
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
@@ -191,6 +194,8 @@ extern "C" int mmd_cg_solve_noalloc(const mmd_csr* A, const double* b, double* x
     g_scratch_addr[dev] = (double*)ptr;
   }
   double* scr = g_scratch_addr[dev];
+  const int max_grid = g_max_grid[dev];
+  setup_lock.unlock();
   cudaStream_t st = (cudaStream_t)stream;
   NAArgs a;
   a.n = A->n;
@@ -212,7 +217,7 @@ extern "C" int mmd_cg_solve_noalloc(const mmd_csr* A, const double* b, double* x
     return MMD_ECUDA;
   }
   int64_t rows_per_block = (A->n + kThreadsNA - 1) / kThreadsNA;
-  int grid = (int)(rows_per_block < g_max_grid[dev] ? rows_per_block : g_max_grid[dev]);
+  int grid = (int)(rows_per_block < max_grid ? rows_per_block : max_grid);
   if (grid < 1) grid = 1;
   void* args[] = {(void*)&a};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)na_cg_kernel, dim3(grid), dim3(kThreadsNA), args, 0, st);
