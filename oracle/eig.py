@@ -34,7 +34,11 @@ notes of the repository):
   mu_mh >= mu_ml alpha / (1 + beta), the ratio of the efficiency condition (ii)
   of Section 6, so the first m_h columns converge even when the coarser level
   stopped on the pair count instead of mu_ex.
-* Lanczos residual: max over all Ritz pairs of T of ||f||_M |e_k^T y_i|.
+* Lanczos residual: ||f||_M |e_k^T y_i| maximised, inside the search loop of
+  Algorithm 4, over the Ritz pairs above the search buffer (all but the d
+  smallest Ritz values of T, the buffer that mu-hat is read from, which the
+  next d-step extension keeps refining) and, in the loop after it (whose
+  Schur vectors are the output), over all Ritz pairs of T.
 * M-QR in Algorithm 5: column-scaled CholQR2 in the M inner product.
 * S = W^T F is symmetrised before its eigen-decomposition (descending).
 * Refinement stop: ||Q_mh - Q'_mh (Q'_mh^T M Q_mh)||_F < eps / sqrt(1 + eps_h delta_h)
@@ -195,10 +199,11 @@ def extend(A, M, Vini, Dini, pcg_tol, res_ok, mu_ex, d, m_tar, opts: EigOpts, ct
     room = n - m0  # Krylov space dimension available
     p = max(1, opts.c_r * d)
 
-    def converge(pp):
+    def converge(pp, skip):
+        # th ascending: the `skip` smallest Ritz values form the search buffer
         for _ in range(opts.max_restarts):
             th, _, res = lz.ritz()
-            if res_ok(th, res):
+            if res_ok(th[skip:], res[skip:]):
                 return
             pp_eff = min(max(pp, lz.j), room - lz.j)
             if pp_eff <= 0:
@@ -214,13 +219,13 @@ def extend(A, M, Vini, Dini, pcg_tol, res_ok, mu_ex, d, m_tar, opts: EigOpts, ct
         steps = min(d, room - lz.j)
         for _ in range(steps):
             lz.step(opfun)
-        converge(p)
+        converge(p, min(d, lz.j - 1))
         th = np.linalg.eigvalsh(lz.T())
         mu_hat = th[min(d, lz.j) - 1]
         if (mu_ex is not None and mu_hat < mu_ex) or lz.j >= m_tar - m0 or lz.j >= room:
             break
     m_new = lz.j
-    converge(max(1, opts.c_r * m_new))
+    converge(max(1, opts.c_r * m_new), 0)
     th, P = np.linalg.eigh(lz.T())
     order = np.argsort(-th, kind="stable")
     th, P = th[order], P[:, order]

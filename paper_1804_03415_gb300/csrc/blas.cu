@@ -49,35 +49,34 @@ __global__ void spmv_kernel(Sell A, const double* __restrict__ x, int64_t ldx, d
       const int32_t base = A.ptr[sl], len = A.len[sl];
       const int32_t row = A.row[sl * 32 + lane];
       double acc[4] = {0, 0, 0, 0};
-      int32_t k = 0;
-      // four entries' loads in flight before their gathers and FMAs (the
-      // FMA order per row is unchanged: entries in CSR order)
-      for (; k + 4 <= len; k += 4) {
-        double a[4];
-        int64_t j[4];
+      // chunks of 8 entries: the loads of a chunk, then its gathers, are in
+      // flight together; the last chunk is cut by a warp-uniform predicate
+      // (len is the slice's), so there is no serial tail.  FMA order per row:
+      // CSR order.
+      for (int32_t k = 0; k < len; k += 8) {
+        double a[8];
+        int64_t j[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 8; ++u) {
           const int32_t o = base + (k + u) * 32 + lane;
-          a[u] = A.val[o];
-          j[u] = A.col[o];
+          if (k + u < len) {
+            a[u] = A.val[o];
+            j[u] = A.col[o];
+          } else {
+            a[u] = 0.0;
+            j[u] = 0;
+          }
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c)
           if (c < mc) {
-            double xv[4];
+            double xv[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) xv[u] = x[j[u] + (c0 + c) * ldx];
+            for (int u = 0; u < 8; ++u) xv[u] = (k + u < len) ? x[j[u] + (c0 + c) * ldx] : 0.0;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) acc[c] = fma(a[u], xv[u], acc[c]);
+            for (int u = 0; u < 8; ++u)
+              if (k + u < len) acc[c] = fma(a[u], xv[u], acc[c]);
           }
-      }
-      for (; k < len; ++k) {
-        const int32_t o = base + k * 32 + lane;
-        const double a = A.val[o];
-        const int64_t j = A.col[o];
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (c < mc) acc[c] = fma(a, x[j + (c0 + c) * ldx], acc[c]);
       }
       if (row >= 0)
         for (int c = 0; c < mc; ++c) y[row + (c0 + c) * ldy] = acc[c];

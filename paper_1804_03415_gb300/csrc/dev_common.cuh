@@ -67,7 +67,7 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& b) {
     unsigned spins = 0;
     while (ld_acquire(b.count) < target) {
       __nanosleep(20);
-      if (((++spins) & 255u) == 0u) {
+      if (((++spins) & 255u) == 1u) {  // first poll, then every 256th
         if (ld_acquire_int(b.status) != DEV_OK || global_ns() - t0 > b.timeout_ns) {
           atomicExch(b.status, (int)DEV_TIMEOUT);
           ok = 0;

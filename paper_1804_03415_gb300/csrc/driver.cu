@@ -630,25 +630,29 @@ ExtendOut extend(Ctx& c, int k, double* BAS, int m0, int cap, const std::vector<
   lz.orth(f, m0);
   const int room = (int)std::min<int64_t>(n - m0, cap - m0);
   const double breakdown = 1e-10;
-  auto res_ok = [&](const std::vector<double>& th, const std::vector<double>& res) {
-    for (size_t i = 0; i < th.size(); ++i) {
+  // Lanczos residual test over the Ritz pairs th[skip..] (th ascending): the
+  // search loop leaves out its buffer of the d smallest Ritz values (the ones
+  // mu-hat is read from, refined by the next extension); the final loop,
+  // whose Schur vectors are the output, tests every pair
+  auto res_ok = [&](const std::vector<double>& th, const std::vector<double>& res, size_t skip) {
+    for (size_t i = skip; i < th.size(); ++i) {
       const double lim = relative ? tol_rel * std::fabs(th[i]) : eps_abs;
       if (!(res[i] <= lim)) return false;
     }
     return true;
   };
-  auto converge = [&](int pp) {
+  auto converge = [&](int pp, int skip) {
     for (int it = 0; it < c.o.max_restarts; ++it) {
       std::vector<double> th, res;
       lz.ritz(th, res);
       if (debug_on()) {
         double worst = 0;
-        for (size_t i = 0; i < th.size(); ++i)
+        for (size_t i = skip; i < th.size(); ++i)
           worst = std::max(worst, res[i] / (relative ? tol_rel * std::fabs(th[i]) : eps_abs));
         fprintf(stderr, "[mmd] level %d converge j=%d worst res/limit=%.3e theta=[%.6e..%.6e]\n", k, lz.j, worst,
                 th.front(), th.back());
       }
-      if (res_ok(th, res)) return;
+      if (res_ok(th, res, (size_t)skip)) return;
       const int pe = std::min(std::max(pp, lz.j), room - lz.j);
       if (pe <= 0) return;
       const int kk = lz.j;
@@ -662,14 +666,14 @@ ExtendOut extend(Ctx& c, int k, double* BAS, int m0, int cap, const std::vector<
   while (true) {
     const int steps = std::min(d, room - lz.j);
     for (int s = 0; s < steps; ++s) lz.step(pcg_tol, breakdown);
-    converge(p);
+    converge(p, std::min(d, lz.j - 1));
     std::vector<double> th;
     lz.tri_eig(lz.j, th, nullptr, nullptr);
     const double mu_hat = th[std::min(d, lz.j) - 1];
     if ((has_mu_ex && mu_hat < mu_ex) || lz.j >= m_tar - m0 || lz.j >= room) break;
   }
   const int m_new = lz.j;
-  converge(std::max(1, c.o.c_r * m_new));
+  converge(std::max(1, c.o.c_r * m_new), 0);
   // Schur form of T: V_ex = [V_ini, V P], eigenvalues descending
   std::vector<double> th;
   double* Y = buf<double>(c.ws, "te_Y", size_t(lz.j) * lz.j);

@@ -121,3 +121,38 @@ def test_entry_points_refuse_host_only_handles_and_bad_options(pkg):
     for bad in ({"peel": -1.0}, {"loc_radius": -1}, {"s_max": 0}):
         with pytest.raises(pkg.MMDError):
             pkg.MMD(A.rowptr, A.col, A.val, device=False, **bad)
+
+
+def test_build_refuses_nonfinite_and_non_spd_inputs(pkg):
+    """Failure paths of mmd_build made on the host: NaN / Inf values ->
+    MMD_EINVAL; a non-positive diagonal, or a positive diagonal whose patch
+    matrix is indefinite -> MMD_ENOTSPD.  Nothing reaches a GPU."""
+    lib = pkg._lib
+    A = W.fd2d(6, seed=W.BASE_SEED + 60)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    off = np.where(rows != A.col)[0]
+    for bad in (np.nan, np.inf, -np.inf):
+        v = A.val.copy()
+        e = off[3]
+        r, c = rows[e], A.col[e]
+        e2 = A.rowptr[c] + np.searchsorted(A.col[A.rowptr[c]:A.rowptr[c + 1]], r)
+        v[e] = v[e2] = bad
+        with pytest.raises(pkg.MMDError) as ei:
+            pkg.MMD(A.rowptr, A.col, v, device=False)
+        assert ei.value.code == lib.MMD_EINVAL
+    v = A.val.copy()
+    d = A.rowptr[5] + np.searchsorted(A.col[A.rowptr[5]:A.rowptr[6]], 5)
+    v[d] = -1.0
+    with pytest.raises(pkg.MMDError) as ei:
+        pkg.MMD(A.rowptr, A.col, v, device=False)
+    assert ei.value.code == lib.MMD_ENOTSPD
+    # I + 2 x (path adjacency): positive diagonal, eigenvalues 1 + 4 cos(pi k / 9) < 0 for some k
+    n = 8
+    i = np.arange(n - 1)
+    P = W.laplacian_from_edges(n, i, i + 1, -2.0 * np.ones(n - 1), 0.0)  # D - W with W = -2
+    val = P.val.copy()
+    rr = np.repeat(np.arange(n), np.diff(P.rowptr))
+    val[rr == P.col] = 1.0
+    with pytest.raises(pkg.MMDError) as ei:
+        pkg.MMD(P.rowptr, P.col, val, device=False, n_coarse=2)
+    assert ei.value.code == lib.MMD_ENOTSPD

@@ -97,3 +97,30 @@ def test_autograd_function():
     lo, Vo = np.linalg.eigh(A.dense())
     go = OG.dLdvals(A, lo[:N], Vo[:, :N], np.ones(N), None)
     assert np.abs(va.grad.cpu().numpy() - go).max() <= 1e-8 * np.abs(go).max()
+
+
+def test_autograd_eigenvector_only_loss_and_second_backward():
+    """A loss that uses V alone (dL/dlambda undefined) goes through backward,
+    matches the oracle's gradient, and a second backward on the retained
+    graph gives the same gradient again."""
+    import paper_1804_03415_gb300 as pkg
+
+    A = W.fd2d(12, seed=W.BASE_SEED + 34)
+    N, k = 5, 1
+    t = np.random.default_rng(5).standard_normal(A.n)
+    rp = torch.from_numpy(A.rowptr).cuda()
+    ci = torch.from_numpy(A.col).cuda()
+    va = torch.from_numpy(A.val).cuda().requires_grad_(True)
+    lam, V = pkg.eigsh_leftmost(rp, ci, va, N, 1e-12, build={"n_coarse": 30})
+    tt = torch.from_numpy(t).cuda()
+    loss = 0.5 * (tt * V[:, k] ** 2).sum()
+    loss.backward(retain_graph=True)
+    g1 = va.grad.detach().clone()
+    lo, Vo = np.linalg.eigh(A.dense())
+    Gvo = np.zeros((A.n, N))
+    Gvo[:, k] = t * Vo[:, k]
+    go = OG.dLdvals(A, lo[:N], Vo[:, :N], np.zeros(N), Gvo, tol=1e-13)
+    assert np.abs(g1.cpu().numpy() - go).max() <= 1e-6 * np.abs(go).max()
+    va.grad = None
+    loss.backward()
+    assert torch.allclose(va.grad, g1, rtol=0, atol=1e-12 * float(g1.abs().max()))

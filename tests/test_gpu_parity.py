@@ -208,20 +208,54 @@ EIG_CASES = {
 }
 
 
+_ORACLE_CACHE = {}
+
+
+def _oracle_eig(name):
+    """The oracle's result for an EIG_CASES entry (computed once per session)."""
+    if name not in _ORACLE_CACHE:
+        make, N, tol, nc = EIG_CASES[name]
+        A = make()
+        ref = OE.eig_leftmost(OM.build(A, OM.BuildOpts(n_coarse=nc)), N, tol)
+        _ORACLE_CACHE[name] = (A, ref, np.linalg.eigvalsh(A.dense()))
+    return _ORACLE_CACHE[name]
+
+
 @pytest.mark.parametrize("name", sorted(EIG_CASES))
 def test_eig_leftmost_matches_oracle(name):
     make, N, tol, nc = EIG_CASES[name]
-    A = make()
-    ref = OE.eig_leftmost(OM.build(A, OM.BuildOpts(n_coarse=nc)), N, tol)
+    A, ref, _ = _oracle_eig(name)
     h = _handle(A, n_coarse=nc)
     lam, V, st = h.eig_leftmost(N, tol)
-    evall = np.linalg.eigvalsh(A.dense())
+    evall = _oracle_eig(name)[2]
     assert_eigpairs_match(lam, V, ref.lam, ref.V, lam_next=evall[N])
     assert st["max_rel_residual"] <= 10 * tol
     assert np.allclose(V.T @ V, np.eye(N), atol=1e-10)
     # also against dense brute force
     ev = evall[:N]
     assert np.abs(lam - ev).max() <= 1e-9 * np.abs(ev).max() + 1e-12 * evall[-1]
+    h.close()
+
+
+@pytest.mark.parametrize("precision", [1, 2], ids=["mixed", "mixed_all"])
+@pytest.mark.parametrize("name", ["fd2d_24", "torus_3000"])
+def test_eig_leftmost_mixed_matches_oracle(name, precision):
+    """MMD_MIXED (FP32 PCG on the coarse levels inside FP64 iterative
+    refinement) and MMD_MIXED_ALL (level-0 CG with FP32 recurrences and FP64
+    reliable updates as well) against the FP64 oracle at the FP64 path's
+    tolerances: every eigenpair within 1e-9 relative, cluster subspaces
+    within cos >= 1 - 1e-12, residual <= 10 tol.  The per-eigenpair errors
+    are in the failure message."""
+    make, N, tol, nc = EIG_CASES[name]
+    A, ref, evall = _oracle_eig(name)
+    h = _handle(A, n_coarse=nc)
+    lam, V, st = h.eig_leftmost(N, tol, precision=precision)
+    rel = np.abs(lam - ref.lam) / np.abs(ref.lam)
+    msg = "per-eigenpair relative error vs the oracle: " + " ".join(f"{x:.1e}" for x in rel)
+    assert rel.max() <= 1e-9, msg
+    assert_eigpairs_match(lam, V, ref.lam, ref.V, lam_next=evall[N])
+    assert st["max_rel_residual"] <= 10 * tol, st["max_rel_residual"]
+    assert np.allclose(V.T @ V, np.eye(N), atol=1e-10)
     h.close()
 
 

@@ -81,6 +81,26 @@ def test_partition_golden():
         assert pr.tolist() == c["patch_rows"], c["name"]
 
 
+def test_neighbourhoods_golden():
+    """Hand-worked psi supports (tests/golden/neighbourhood_cases.json): the
+    one-ring ranking by connection count, a tie resolved to the lowest patch
+    id, a patch skipped for omega_max with the next one still taken, and the
+    ascending second ring."""
+    g = json.load(open(os.path.join(GOLDEN, "neighbourhood_cases.json")))
+    e = np.array(g["edges"])
+    n = g["n"]
+    A = W.laplacian_from_edges(n, e[:, 0], e[:, 1], np.ones(len(e)), 0.1).to_scipy()
+    po = np.array(g["patch_of"], np.int32)
+    npatch = int(po.max()) + 1
+    ptr = np.zeros(npatch + 1, np.int32)
+    ptr[1:] = np.cumsum(np.bincount(po))
+    rows = np.lexsort((np.arange(n), po)).astype(np.int32)
+    for c in g["cases"]:
+        optr, orows = MM.neighbourhoods(A, po, ptr, rows, c["omega_max"], c["loc_radius"])
+        got = [[int(r) for r in orows[optr[j]:optr[j + 1]]] for j in range(npatch)]
+        assert got == c["omega"], c["name"]
+
+
 @pytest.mark.parametrize("seed", [1, 2, 3])
 def test_partition_properties(seed):
     A = W.random_spd_mmatrix(300, 6.0, seed)
