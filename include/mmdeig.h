@@ -49,6 +49,13 @@ extern "C" {
 #define MMD_ECUDA (-5)    /* a CUDA runtime call failed */
 #define MMD_ENOMEM (-6)   /* host or device allocation failed */
 
+/* methods of eig_leftmost */
+#define MMD_HIERARCHICAL 0 /* Algorithm 6 on the decomposition (the paper's method) */
+#define MMD_IRLM_CG 1      /* Section 8's baseline: implicitly restarted Lanczos on A^{-1}, each
+                              application by plain CG, no decomposition (the extension of
+                              Algorithm 4 at level 0 from an empty basis with searching step
+                              d = N, i.e. N wanted and N shifts per restart) */
+
 /* precision modes of eig_leftmost */
 #define MMD_FP64 0      /* every step in FP64 */
 #define MMD_MIXED 1     /* coarse levels k >= 1: FP32 PCG inside FP64 iterative
@@ -98,6 +105,13 @@ typedef struct {
   uint64_t seed;       /* SplitMix64 seed of the random vectors drawn */
   void* stream;        /* cudaStream_t */
   int profile;         /* 1: time every launch of the PCG kernel with events */
+  int method;          /* MMD_HIERARCHICAL (default) or MMD_IRLM_CG */
+  int stop_level;      /* MMD_HIERARCHICAL: the last level Algorithm 6 computes (default 0: the
+                          level-0 completion, residual target tol).  s >= 1 ends at level s with
+                          its own accuracy eps_s (Lemma 3.3) and returns V = Psi^(1)...Psi^(s) V^(s):
+                          s = 1 is Algorithm 6's own output, s = K the dense solve of the coarsest
+                          pencil (Section 7.2); the last level extends to N pairs without the
+                          extension threshold.  Must be <= K. */
 } mmd_eig_opts;
 
 /* Counters and timings of one eig_leftmost call (Section 7 reports the same

@@ -69,6 +69,8 @@ class EigOpts:
     max_refine_iter: int = 100
     seed: int = 20180409
     breakdown: float = 1e-10
+    method: str = "hierarchical"  # or "irlm_cg": Section 8's baseline (no decomposition)
+    stop_level: int = 0  # last level computed; s >= 1 returns Psi^(1)...Psi^(s) V^(s) (accuracy eps_s)
 
 
 @dataclasses.dataclass
@@ -320,6 +322,21 @@ def eig_leftmost(D: _mmd.MMD, N: int, tol: float, opts: EigOpts | None = None) -
     if N < 1 or N > n:
         raise ValueError("N out of range")
     lstats = []
+    if opts.method == "irlm_cg":
+        # Section 8's baseline: implicitly restarted Lanczos on A^{-1}, every
+        # application by plain CG, no decomposition.  Algorithm 4 at level 0
+        # from an empty basis with searching step d = N: one extension reaches
+        # N columns and each restart of the final loop applies N exact shifts.
+        st = LevelStats(0, n)
+        A0 = D.A(0)
+        Vh, Dh = extend(A0, None, np.zeros((n, 0)), np.zeros(0), 0.1 * tol,
+                        lambda th, res: bool(np.all(res <= tol * np.abs(th))), None, N, N, opts, ctr, st, 1000)
+        lstats.append(st)
+        order = np.argsort(-Dh, kind="stable")[:N]
+        return _finish(1.0 / Dh[order], Vh[:, order], ctr, lstats, 0.0)
+    if not 0 <= opts.stop_level <= K:
+        raise ValueError("stop_level out of range")
+    last = opts.stop_level
     # coarsest level: (A^(K))^{-1} M^(K) x = mu x  <=>  A^(K) x = lambda M^(K) x
     AK = D.A(K).toarray()
     MK = np.eye(AK.shape[0]) if K == 0 else D.M(K).toarray()
@@ -330,12 +347,15 @@ def eig_leftmost(D: _mmd.MMD, N: int, tol: float, opts: EigOpts | None = None) -
         V, lam_out = Z[:, :N], 1.0 / mu[:N]
         return _finish(lam_out, V, ctr, lstats, mu1)
     epsK = D.levels[K - 1].eps
-    keep = min(int(np.sum(mu >= opts.beta * epsK)), N)
+    if last == K:  # the coarse-level approximation (Section 7.2): the N largest mu of the pencil
+        keep = min(len(mu), N)
+    else:
+        keep = min(int(np.sum(mu >= opts.beta * epsK)), N)
     Vh, Dh = Z[:, :keep], mu[:keep]
     lstats.append(LevelStats(K, D.N(K), m_extended=keep))
     trace = [(K, Dh.copy())]
     stream = 1000
-    for k in range(K - 1, -1, -1):
+    for k in range(K - 1, last - 1, -1):
         st = LevelStats(k, D.N(k))
         lev_l = D.levels[k]  # level k + 1 (its patches partition level k)
         Vh = lev_l.psi @ Vh  # Algorithm 6, coefficient transfer
@@ -347,7 +367,7 @@ def eig_leftmost(D: _mmd.MMD, N: int, tol: float, opts: EigOpts | None = None) -
             tol_rel = float(np.clip(0.1 * eps_h / mu1, 1e-14, 0.1))
             eps_abs = 0.1 * eps_h
             res_ok = lambda th, res, e=eps_abs: bool(np.all(res <= e))
-            mu_ex = opts.beta * eps_h
+            mu_ex = opts.beta * eps_h if k > last else None  # the last level extends to N pairs
         else:
             eps_h, delta_h = 0.0, 0.0
             tol_rel = tol
@@ -361,6 +381,9 @@ def eig_leftmost(D: _mmd.MMD, N: int, tol: float, opts: EigOpts | None = None) -
         stream += 1000
         lstats.append(st)
         trace.append((k, Dh.copy()))
+    # a result on level s >= 1: V = Psi^(1) ... Psi^(s) V^(s) (Algorithm 6, last line)
+    for j in range(last, 0, -1):
+        Vh = D.levels[j - 1].psi @ Vh
     order = np.argsort(-Dh, kind="stable")[:N]
     res = _finish(1.0 / Dh[order], Vh[:, order], ctr, lstats, mu1)
     res.trace = trace

@@ -16,7 +16,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import MMD_FP64, MMD_MIXED, MMD_MIXED_ALL, MMDError  # noqa: F401
+from ._lib import MMD_FP64, MMD_HIERARCHICAL, MMD_IRLM_CG, MMD_MIXED, MMD_MIXED_ALL, MMDError  # noqa: F401
 
 
 def build_opts(**kw) -> _lib.mmd_build_opts:

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libmmdeig.so")
 
 MMD_OK, MMD_EINVAL, MMD_ENOTSPD, MMD_ENOCONV, MMD_ETIMEOUT, MMD_ECUDA, MMD_ENOMEM = 0, -1, -2, -3, -4, -5, -6
 MMD_FP64, MMD_MIXED, MMD_MIXED_ALL = 0, 1, 2
+MMD_HIERARCHICAL, MMD_IRLM_CG = 0, 1
 
 i32p = C.POINTER(C.c_int32)
 f64p = C.POINTER(C.c_double)
@@ -34,7 +35,7 @@ class mmd_eig_opts(C.Structure):
     _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("d", C.c_int), ("c_r", C.c_int),
                 ("precision", C.c_int), ("max_cg_iter", C.c_int), ("max_restarts", C.c_int),
                 ("max_refine_iter", C.c_int), ("timeout_s", C.c_double), ("seed", C.c_uint64),
-                ("stream", C.c_void_p), ("profile", C.c_int)]
+                ("stream", C.c_void_p), ("profile", C.c_int), ("method", C.c_int), ("stop_level", C.c_int)]
 
 
 class mmd_eig_stats(C.Structure):

@@ -266,6 +266,8 @@ void mmd_default_eig_opts(mmd_eig_opts* o) {
   o->seed = 20180409ull;
   o->stream = nullptr;
   o->profile = 0;
+  o->method = MMD_HIERARCHICAL;
+  o->stop_level = 0;
 }
 
 int mmd_build(const mmd_csr* A, const mmd_build_opts* opts, mmd_handle** out) {
@@ -454,6 +456,10 @@ static bool validated_opts(const mmd_eig_opts* opts, const char* who, mmd_eig_op
   else if (!(o.timeout_s > 0) || !std::isfinite(o.timeout_s)) bad = "timeout_s must be finite and > 0";
   else if (o.precision != MMD_FP64 && o.precision != MMD_MIXED && o.precision != MMD_MIXED_ALL)
     bad = "precision must be MMD_FP64, MMD_MIXED or MMD_MIXED_ALL";
+  else if (o.method != MMD_HIERARCHICAL && o.method != MMD_IRLM_CG)
+    bad = "method must be MMD_HIERARCHICAL or MMD_IRLM_CG";
+  else if (o.stop_level < 0 || o.stop_level > 16) bad = "stop_level must be in [0, K]";
+  else if (o.method == MMD_IRLM_CG && o.stop_level != 0) bad = "stop_level applies to MMD_HIERARCHICAL only";
   if (!bad.empty()) {
     set_error(std::string(who) + ": invalid options: " + bad);
     return false;

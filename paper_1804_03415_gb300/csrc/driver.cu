@@ -1067,6 +1067,32 @@ int run_eig(mmd_handle* h, int N, double tol, const mmd_eig_opts& o, double* lam
       int* iwork = buf<int>(c.ws, "tri_iwork", size_t(tri_max) * tri_max);
       set_tri_scratch(bounds, e2, cst, ncl, work, iwork);
     }
+    if (o.stop_level > K) {
+      set_error("eig_leftmost: stop_level " + std::to_string(o.stop_level) + " exceeds the handle's K = " +
+                std::to_string(K));
+      throw CudaFail{MMD_EINVAL};
+    }
+    std::vector<double> D;
+    int m = 0;
+    double* Vh = nullptr;
+    int out_level = 0;  // the level whose coefficient vectors Vh holds at the end
+    if (o.method == MMD_IRLM_CG) {
+      // Section 8's baseline: no decomposition; Algorithm 4 at level 0 from an
+      // empty basis with searching step d = N, so one extension reaches N
+      // columns and each restart of its final loop applies N exact shifts
+      // (N wanted pairs, 2N Lanczos vectors); OP is plain CG on A.
+      const int64_t n = h->dl[0].n;
+      const int d = N;
+      const int cap = (int)std::min<int64_t>(n, 2 * ((int64_t)N + d) + 8);
+      double* BAS = buf<double>(c.ws, "BAS_b", size_t(n) * cap);
+      ExtendOut ex = extend(c, 0, BAS, 0, cap, std::vector<double>(), 0.1 * tol, true, 0.0, tol, false, 0.0, d, N,
+                            1000);
+      m = ex.m;
+      D = ex.D;
+      Vh = BAS;
+      c.sync();
+      S_level_mark(c, 0, t0);
+    } else {
     // ---- coarsest level (Algorithm 6, first step)
     std::vector<double> mu;
     const int nK = (int)h->dl[K].n;
@@ -1074,9 +1100,7 @@ int run_eig(mmd_handle* h, int N, double tol, const mmd_eig_opts& o, double* lam
     coarsest(c, K, mu, Z);
     c.S.mu1 = mu.empty() ? 0.0 : mu[0];
     const double mu1 = c.S.mu1;
-    std::vector<double> D;
-    int m = 0;
-    double* Vh = nullptr;
+    const int last = o.stop_level;  // the last level computed
     if (K == 0) {
       m = std::min(N, nK);
       D.assign(mu.begin(), mu.begin() + m);
@@ -1085,7 +1109,11 @@ int run_eig(mmd_handle* h, int N, double tol, const mmd_eig_opts& o, double* lam
     } else {
       const double epsK = h->dl[K].eps;
       int keep = 0;
-      while (keep < (int)mu.size() && mu[keep] >= o.beta * epsK) ++keep;
+      if (last == K) {
+        keep = (int)mu.size();  // the coarse-level approximation: the N largest mu of the pencil
+      } else {
+        while (keep < (int)mu.size() && mu[keep] >= o.beta * epsK) ++keep;
+      }
       m = std::min(keep, N);
       D.assign(mu.begin(), mu.begin() + m);
       Vh = buf<double>(c.ws, "V_cur", size_t(nK) * std::max(m, 1));
@@ -1093,7 +1121,7 @@ int run_eig(mmd_handle* h, int N, double tol, const mmd_eig_opts& o, double* lam
       uint64_t stream = 1000;
       c.sync();
       if (K < 16) S_level_mark(c, K, t0);
-      for (int k = K - 1; k >= 0; --k) {
+      for (int k = K - 1; k >= last; --k) {
         const DLevel& L = h->dl[k];
         const int64_t n = L.n;
         const int d = o.d > 0 ? o.d : std::max(1, (int)std::min<int64_t>(n / 10, N / 10));
@@ -1122,8 +1150,8 @@ int run_eig(mmd_handle* h, int N, double tol, const mmd_eig_opts& o, double* lam
         const double mu_re = o.alpha * eps_l;
         // Algorithm 5: refined pairs into BAS[:, :mh]
         int mh = refine(c, k, Q0, D, pcg_tol, mu_re, eps_h, delta_h, BAS);
-        // Algorithm 4
-        ExtendOut ex = extend(c, k, BAS, mh, cap, D, pcg_tol, relative, eps_abs, tol, k >= 1,
+        // Algorithm 4; the last level computed extends to N pairs (no extension threshold)
+        ExtendOut ex = extend(c, k, BAS, mh, cap, D, pcg_tol, relative, eps_abs, tol, k > last,
                               o.beta * eps_h, d, N, stream);
         stream += 1000;
         m = ex.m;
@@ -1132,6 +1160,15 @@ int run_eig(mmd_handle* h, int N, double tol, const mmd_eig_opts& o, double* lam
         c.sync();
         if (k < 16) S_level_mark(c, k, t0);
       }
+      out_level = last;
+    }
+    }
+    // a result on level s >= 1: V = Psi^(1) ... Psi^(s) V^(s) (Algorithm 6, last line)
+    for (int j = out_level; j >= 1 && m > 0; --j) {
+      double* T = buf<double>(c.ws, j % 2 ? "xfer_a" : "xfer_b", size_t(h->dl[j - 1].n) * m);
+      k_spmv(sell_of(h->dl[j].psi), Vh, h->dl[j].n, T, h->dl[j - 1].n, m, st);
+      c.after_launch();
+      Vh = T;
     }
     // ---- outputs: N largest mu -> ascending lambda, natural order, normalised
     std::vector<int> order(m);

@@ -284,3 +284,56 @@ def test_eig_device_outputs_and_edge_cases():
     lam, V, st = h.eig_leftmost(36, 1e-10)
     assert np.allclose(lam, np.linalg.eigvalsh(B.dense()), rtol=1e-9)
     h.close()
+
+
+@pytest.mark.parametrize("name", ["fd2d_24", "torus_3000"])
+def test_irlm_cg_baseline_matches_oracle(name):
+    """MMD_IRLM_CG (Section 8's baseline: implicitly restarted Lanczos with
+    plain CG, no decomposition) reaches the same defined result as the
+    oracle, at the tolerances of the hierarchical path."""
+    pkg = _pkg()
+    make, N, tol, nc = EIG_CASES[name]
+    A, ref, evall = _oracle_eig(name)
+    h = _handle(A, n_coarse=nc)
+    lam, V, st = h.eig_leftmost(N, tol, method=pkg.MMD_IRLM_CG)
+    assert_eigpairs_match(lam, V, ref.lam, ref.V, lam_next=evall[N])
+    assert st["max_rel_residual"] <= 10 * tol
+    assert st["refine_iters"] == 0 and st["lanczos_steps"] >= N
+    h.close()
+
+
+def test_stop_level_matches_oracle():
+    """Algorithm 6 ended at level s: s = K (dense coarsest pencil, Section
+    7.2) equals the oracle's eigenpairs to 1e-10 (same pencil, same dense
+    problem); s = 1 (Algorithm 6's own output V = Psi^(1) V^(1)) puts every
+    mu within the level's Lanczos accuracy 0.1 eps_1 of the exact level-1
+    pencil, as the oracle's does, and both lie within 1.1 eps_1 of the true
+    mu (exact Psi at level 1: supports covering every patch)."""
+    pkg = _pkg()
+    A = W.fd2d(32, seed=W.BASE_SEED + 93, log10_range=(-0.5, 0.5))
+    N = 6
+    bo = dict(n_coarse=12, k_max=2, loc_radius=50, omega_max=10**6)
+    D = OM.build(A, OM.BuildOpts(**bo))
+    h = _handle(A, **bo)
+    assert h.num_levels == D.K == 2
+    ev = np.linalg.eigvalsh(A.dense())
+    eps1 = D.levels[0].eps
+    for s in (2, 1):
+        ref = OE.eig_leftmost(D, N, 1e-10, OE.EigOpts(stop_level=s))
+        lam, V, st = h.eig_leftmost(N, 1e-10, stop_level=s, allow_noconv=True)
+        assert st["not_converged"] == 0
+        if s == 2:
+            assert np.allclose(lam, ref.lam, rtol=1e-10)
+            sv = np.linalg.svd(V.T @ ref.V, compute_uv=False)
+            assert sv.min() >= 1 - 1e-10
+        else:
+            import scipy.linalg as sla
+
+            mu1 = 1.0 / sla.eigh(D.A(1).toarray(), D.M(1).toarray(), eigvals_only=True)[:N]
+            assert np.abs(1.0 / lam - mu1).max() <= 0.1 * eps1
+            assert np.abs(1.0 / ref.lam - mu1).max() <= 0.1 * eps1
+            assert np.abs(1.0 / lam - 1.0 / ev[:N]).max() <= 1.1 * eps1
+        assert np.allclose(V.T @ V, np.eye(N), atol=1e-9)
+    with pytest.raises(pkg.MMDError):
+        h.eig_leftmost(N, 1e-10, stop_level=3)
+    h.close()

@@ -411,3 +411,62 @@ def test_gradient_block_plus_complement_matches_dense():
     g0 = OG.dLdvals(Acsr, lam[:N], V[:, :N], gl, None)
     G0 = (V[:, :N] * gl) @ V[:, :N].T
     assert np.allclose(g0, G0[rows, Acsr.col], atol=1e-13)
+
+
+def test_reference_shift_invert_matches_dense():
+    """The independent large-n check (shift-invert Lanczos) against dense
+    LAPACK on a shifted graph Laplacian with a cluster of zero modes and on
+    an FD operator."""
+    from oracle import reference as RF
+
+    for A, N in ((W.rgg(900, deg=8.0, seed=W.BASE_SEED + 90), 30), (W.fd2d(20, seed=W.BASE_SEED + 91), 25)):
+        lam, V = RF.leftmost_shift_invert(A.to_scipy(), N)
+        ev = np.linalg.eigvalsh(A.dense())[:N]
+        assert np.abs(lam - ev).max() <= 1e-11 * np.abs(ev).max() + 1e-13 * np.abs(A.val).max()
+        R = A.to_scipy() @ V - V * lam
+        assert np.linalg.norm(R, axis=0).max() <= 1e-9 * np.abs(A.val).max()
+
+
+def test_irlm_cg_baseline_matches_dense():
+    """Section 8's baseline (implicitly restarted Lanczos on A^{-1} by plain
+    CG, no decomposition) reaches the defined result: the N smallest
+    eigenpairs of dense LAPACK, residual <= tol, orthonormal vectors."""
+    A = W.fd2d(20, seed=W.BASE_SEED + 92)
+    D = MM.build(A, MM.BuildOpts(n_coarse=40))
+    r = E.eig_leftmost(D, 12, 1e-10, E.EigOpts(method="irlm_cg"))
+    ev = np.linalg.eigvalsh(A.dense())
+    assert np.abs(r.lam - ev[:12]).max() <= 1e-9 * np.abs(ev[:12]).max()
+    assert E.residuals(A.to_scipy(), r.lam, r.V).max() <= 10 * 1e-10 * ev[-1]
+    assert np.allclose(r.V.T @ r.V, np.eye(12), atol=1e-9)
+    assert len(r.levels) == 1 and r.levels[0].lanczos_steps >= 12
+
+
+def test_stop_level_coarse_approximation_bounds():
+    """Algorithm 6 ended at level s returns Psi^(1)...Psi^(s) V^(s).  With the
+    exact Psi at level 1 (supports covering every patch, Section 2.3)
+    Theorem 2.1 gives ||A^{-1} - Theta^(1)|| <= eps(P^(1)), so the returned
+    mu_i are within eps_1 of the true mu_i (Weyl), plus the level's Lanczos
+    accuracy 0.1 eps_1 when level 1 runs an extension (s = 1 < K), and the
+    residual ||A^{-1} v - mu v|| stays within 2 eps_1 (Section 7.2);
+    Courant-Fischer: lambda-tilde >= lambda.  s = K is the dense solve of the
+    coarsest pencil (Section 7.2), equal to LAPACK on that pencil.  The
+    coefficients are random so that the spectrum has no exact multiplicity."""
+    A = W.fd2d(32, seed=W.BASE_SEED + 93, log10_range=(-0.5, 0.5))
+    Ad = A.dense()
+    Ai = np.linalg.inv(Ad)
+    ev = np.linalg.eigvalsh(Ad)
+    N = 6
+    for kmax, s in ((1, 1), (2, 1)):
+        D = MM.build(A, MM.BuildOpts(n_coarse=12, k_max=kmax, loc_radius=50, omega_max=10**6))
+        assert D.K == kmax and D.N(D.K) >= N
+        eps1 = D.levels[0].eps
+        r = E.eig_leftmost(D, N, 1e-10, E.EigOpts(stop_level=s))
+        assert np.all(r.lam >= ev[:N] * (1 - 1e-10))
+        slack = 1.0 if s == D.K else 1.1
+        assert np.all(np.abs(1 / r.lam - 1 / ev[:N]) <= slack * eps1)
+        assert np.linalg.norm(Ai @ r.V - r.V / r.lam, axis=0).max() <= (2.0 + slack - 1.0) * eps1
+        assert np.allclose(r.V.T @ r.V, np.eye(N), atol=1e-9)
+        if s == D.K:
+            lamK = sla.eigh(D.A(s).toarray(), D.M(s).toarray(), eigvals_only=True)[:N]
+            assert np.allclose(r.lam, lamK, rtol=1e-11)
+            assert np.allclose(np.einsum("ij,ij->j", r.V, Ad @ r.V), r.lam, rtol=1e-10)
