@@ -382,10 +382,14 @@ def spmv_bench(G, W, torch, sptr, peak):
     same = bool(torch.equal(y, y2))
     byts = 12.0 * A.nnz + 20.0 * A.n
     gbs = byts / (ms / 1e3) / 1e9
+    variant, vms = h.spmv_tuning(0, 0)
     h.close()
     return {"matrix": "fd3d 128^3 7-point, n=2097152, nnz=14581760, FP64", "ms": ms, "GB_s": gbs,
             "frac_of_hbm": gbs / peak, "bytes_per_call": byts, "bit_identical_to_level_spmv": same,
-            "bytes": "12 nnz + 20 n (values, columns, row pointers, x once, y)"}
+            "bytes": "12 nnz + 20 n (values, columns, row pointers, x once, y)",
+            "autotune": {"chosen_variant": variant, "ms_per_variant": vms,
+                         "variants": "entries in flight / block size / min blocks per SM: 4/128/10, 4/256/5, "
+                                     "8/128/8, 8/256/4, 8/512/2, 16/128/4"}}
 
 
 # ------------------------------------------------------------------ distributed helpers
@@ -454,6 +458,23 @@ def kernel_case(which: str):
         st = h.eig_leftmost(WORKLOAD["N"], WORKLOAD["tol"], allow_noconv=True)[2]
         print(json.dumps({"kernel_case": "eig", "kernel_launches": st["kernel_launches"],
                           "n_converged": st["n_converged"]}))
+    elif which == "vcycle":
+        # V-cycle preconditioner of the level-0 refinement on the torus 200k levels:
+        # 20 applications to 4 columns, event-timed, and one warm-started refinement-type
+        # PCG solve of 4 columns with and without it
+        A = W.torus_knn(WORKLOAD["n"], k=WORKLOAD["k"], seed=W.BASE_SEED + 1)
+        h = G.MMD(A.rowptr, A.col, A.val)
+        R = torch.rand((4, A.n), dtype=torch.float64, device="cuda")
+        Z = torch.empty_like(R)
+        h.level_vcycle(R, Z)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(20):
+            h.level_vcycle(R, Z)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_case": "vcycle", "ms_per_vcycle_4cols": e0.elapsed_time(e1) / 20}))
     elif which == "block":
         A = W.torus_knn(WORKLOAD["n"], k=WORKLOAD["k"], seed=W.BASE_SEED + 1)
         h = G.MMD(A.rowptr, A.col, A.val, k_max=1)
@@ -486,7 +507,7 @@ def main():
     ap.add_argument("--no-irlm", action="store_true", help="skip the IRLM-CG baseline step")
     ap.add_argument("--budget-s", type=float, default=1500.0,
                     help="wall-clock budget of the run; optional legs are skipped past it")
-    ap.add_argument("--kernel-case", choices=["op", "block", "eig", "spmv"], default=None)
+    ap.add_argument("--kernel-case", choices=["op", "block", "eig", "spmv", "vcycle"], default=None)
     args = ap.parse_args()
     if args.oracle_worker:
         oracle_sample_worker(args.oracle_worker)

@@ -112,6 +112,11 @@ typedef struct {
                           s = 1 is Algorithm 6's own output, s = K the dense solve of the coarsest
                           pencil (Section 7.2); the last level extends to N pairs without the
                           extension threshold.  Must be <= K. */
+  int mg_refine;       /* level-0 refinement solves (Algorithm 5, warm-started PCG on A) use the
+                          decomposition as a preconditioner (Section 2.3's A^{-1} representation
+                          applied as an FP32 V-cycle over the levels, Chebyshev smoothing of this
+                          degree; the outer PCG stays FP64 with the same stopping test).  0 = plain
+                          CG.  Default 2.  Lanczos OP solves keep plain CG (Section 4). */
 } mmd_eig_opts;
 
 /* Counters and timings of one eig_leftmost call (Section 7 reports the same
@@ -255,6 +260,26 @@ int mmd_level_op_block(mmd_handle* h, int k, int m, const double* X, double* Y, 
                        int64_t* iters, int precision, void* stream);
 int mmd_level_bsolve(mmd_handle* h, int k, const double* q, double* x, double tol, int max_iter,
                      int64_t* iters, void* stream);
+/* mmd_level_vcycle: Z = V(R) for m columns of level 0 (n x m, column-major,
+ *   device memory, natural order): one application of the V-cycle
+ *   preconditioner of mg_refine (Section 2.3's representation A^{-1} =
+ *   U B^{-1} U^T + Psi (Psi^T A Psi)^{-1} Psi^T applied level by level:
+ *   Chebyshev smoothing of degree deg (>= 1) with D^{-1} A^(k) on
+ *   [hi / 30, hi], hi the Gershgorin bound, restriction Psi^T, recursion,
+ *   prolongation Psi, smoothing again; the coarsest level by its dense
+ *   inverse), FP32 arithmetic, FP64 in and out.  Needs K >= 1 and a coarsest
+ *   level of at most 2048 rows (else MMD_EINVAL). */
+int mmd_level_vcycle(mmd_handle* h, int m, const double* R, double* Z, int deg, void* stream);
+
+/* The SpMV autotuner: when a level matrix is uploaded the library times each
+ * single-column SELL SpMV kernel variant on it (entries in flight per lane
+ * 4 / 8 / 16, blocks of 128 / 256 / 512 threads, register bounds; five
+ * launches each after a warm-up) and uses the fastest for that matrix.
+ * Returns the chosen variant of A^(k) (which = 0) or M^(k) (which = 1, k >= 1)
+ * and writes every variant's mean time in ms to ms_per_variant (MMD_SPMV_VARIANTS
+ * entries) unless it is NULL; MMD_EINVAL on bad arguments. */
+#define MMD_SPMV_VARIANTS 6
+int mmd_spmv_tuning(const mmd_handle* h, int k, int which, float* ms_per_variant);
 
 void mmd_free(mmd_handle* h);
 const char* mmd_strerror(int code);

@@ -44,7 +44,9 @@ notes of the repository):
 * Refinement stop: ||Q_mh - Q'_mh (Q'_mh^T M Q_mh)||_F < eps / sqrt(1 + eps_h delta_h)
   (the stricter of the two forms in Section 5).
 * Coarsest level: keep the pairs with mu >= beta eps_K, at most m_tar.
-* d = max(1, min(floor(N^(k)/10), floor(m_tar/10))) (Section 6).
+* d = max(1, min(floor(N^(k)/10), floor(m_tar/10))) (Section 6) on levels with an
+  extension threshold; where there is none (level 0, the last level computed)
+  the searching step has nothing to search and d = m_tar - dim V_ini.
 """
 from __future__ import annotations
 
@@ -194,6 +196,11 @@ def extend(A, M, Vini, Dini, pcg_tol, res_ok, mu_ex, d, m_tar, opts: EigOpts, ct
     n = A.shape[0]
     if n - m0 <= 0:
         return Vini, Dini
+    if mu_ex is None and opts.d == 0:
+        # no extension threshold (level 0, or the last level computed): the
+        # searching step only serves the test of mu-hat against mu_ex (Section
+        # 6), so one extension goes straight to the target
+        d = max(1, m_tar - m0)
     r = _rng.uniform_pm1(opts.seed, stream0, n)
     lz = Lanczos(M, Vini, r, opts.seed, stream0 + 1, opts.breakdown)
     lz.f = lz.orth(r)

@@ -131,6 +131,20 @@ class MMD:
                                                 precision, stream), "mmd_level_op_block")
         return list(its)
 
+    def spmv_tuning(self, k=0, which=0):
+        """(chosen single-column SpMV variant, ms of every variant) of A^(k) / M^(k)."""
+        ms = (C.c_float * _lib.MMD_SPMV_VARIANTS)()
+        v = self._lib.mmd_spmv_tuning(self.h, k, which, ms)
+        if v < 0:
+            _lib.check(v, "mmd_spmv_tuning")
+        return v, [float(x) for x in ms]
+
+    def level_vcycle(self, R, Z, deg=2, stream=0):
+        """Z = V(R): one application of the level-0 V-cycle preconditioner;
+        R, Z: CUDA float64 tensors (m, n), one row per column."""
+        _lib.check(self._lib.mmd_level_vcycle(self.h, R.shape[0], R.data_ptr(), Z.data_ptr(), deg, stream),
+                   "mmd_level_vcycle")
+
     def level_bsolve(self, k, q, x, tol, max_iter=20000, stream=0) -> int:
         it = C.c_int64(0)
         _lib.check(self._lib.mmd_level_bsolve(self.h, k, q.data_ptr(), x.data_ptr(), tol, max_iter, C.byref(it),

@@ -35,7 +35,8 @@ class mmd_eig_opts(C.Structure):
     _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("d", C.c_int), ("c_r", C.c_int),
                 ("precision", C.c_int), ("max_cg_iter", C.c_int), ("max_restarts", C.c_int),
                 ("max_refine_iter", C.c_int), ("timeout_s", C.c_double), ("seed", C.c_uint64),
-                ("stream", C.c_void_p), ("profile", C.c_int), ("method", C.c_int), ("stop_level", C.c_int)]
+                ("stream", C.c_void_p), ("profile", C.c_int), ("method", C.c_int), ("stop_level", C.c_int),
+                ("mg_refine", C.c_int)]
 
 
 class mmd_eig_stats(C.Structure):
@@ -85,6 +86,8 @@ SIGNATURES = {
                                C.POINTER(C.c_int64), C.c_void_p]),
     "mmd_level_op_block": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                      C.c_void_p, C.c_int, C.c_void_p]),
+    "mmd_spmv_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "mmd_level_vcycle": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "mmd_level_bsolve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                    C.POINTER(C.c_int64), C.c_void_p]),
     "mmd_free": (None, [C.c_void_p]),
@@ -95,6 +98,7 @@ SIGNATURES = {
 }
 
 MMD_NOALLOC_MAX_N = 262144
+MMD_SPMV_VARIANTS = 6
 
 _lib = None
 

@@ -87,6 +87,39 @@ static HCSR permute_rect(const HCSR& A, const std::vector<int32_t>& prow, const 
   return B;
 }
 
+// Pick the single-column SpMV kernel of this matrix by timing every variant
+// on it (the autotuner; a few launches per variant on scratch vectors).
+static int autotune_spmv(DCSR& D) {
+  if (D.nrows < 1 || D.ncols < 1) return MMD_OK;
+  double *x = nullptr, *y = nullptr;
+  if (cudaMalloc(&x, sizeof(double) * D.ncols) != cudaSuccess ||
+      cudaMalloc(&y, sizeof(double) * D.nrows) != cudaSuccess) {
+    cudaFree(x);
+    cudaGetLastError();
+    set_error("cudaMalloc of the SpMV autotuner's vectors failed");
+    return MMD_ENOMEM;
+  }
+  cudaMemset(x, 0, sizeof(double) * D.ncols);
+  Sell s;
+  s.nrows = D.nrows;
+  s.nslices = D.nslices;
+  s.ptr = D.s_ptr;
+  s.len = D.s_len;
+  s.row = D.s_row;
+  s.col = D.s_col;
+  s.val = D.s_val;
+  s.val32 = D.s_val32;
+  D.spmv_ms.assign(k_spmv_variants(), 0.f);
+  D.spmv_variant = k_spmv_autotune(s, x, y, nullptr, D.spmv_ms.data());
+  cudaFree(x);
+  cudaFree(y);
+  if (cudaDeviceSynchronize() != cudaSuccess || D.spmv_variant < 0) {
+    set_error("the SpMV autotuner's launches failed");
+    return MMD_ECUDA;
+  }
+  return MMD_OK;
+}
+
 static int upload_csr(const HCSR& A, DCSR& D) {
   D.nrows = A.nrows;
   D.ncols = A.ncols;
@@ -157,7 +190,80 @@ static int upload_csr(const HCSR& A, DCSR& D) {
   if ((rc = dput(&D.s_val, sval))) return rc;
   std::vector<float> sv32(sval.begin(), sval.end());
   if ((rc = dput(&D.s_val32, sv32))) return rc;
-  return MMD_OK;
+  return autotune_spmv(D);
+}
+
+// largest coarsest level whose dense inverse is formed for the V-cycle
+constexpr int64_t kMgMaxCoarse = 2048;
+
+static HCSR transpose(const HCSR& A) {
+  HCSR T;
+  T.nrows = A.ncols;
+  T.ncols = A.nrows;
+  T.rowptr.assign(T.nrows + 1, 0);
+  for (int32_t c : A.col) ++T.rowptr[c + 1];
+  for (int64_t i = 0; i < T.nrows; ++i) T.rowptr[i + 1] += T.rowptr[i];
+  T.col.resize(A.col.size());
+  T.val.resize(A.val.size());
+  std::vector<int32_t> fill(T.rowptr.begin(), T.rowptr.end() - 1);
+  for (int64_t r = 0; r < A.nrows; ++r)  // rows ascending: columns of T come out sorted
+    for (int32_t k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k) {
+      const int32_t o = fill[A.col[k]]++;
+      T.col[o] = (int32_t)r;
+      T.val[o] = A.val[k];
+    }
+  return T;
+}
+
+// max_i sum_j |a_ij| / a_ii: the Gershgorin bound of lambda_max(D^{-1} A)
+static double gershgorin(const HCSR& A) {
+  double g = 0;
+  for (int64_t r = 0; r < A.nrows; ++r) {
+    double s = 0, d = 0;
+    for (int32_t k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k) {
+      s += std::fabs(A.val[k]);
+      if (A.col[k] == r) d = A.val[k];
+    }
+    if (d > 0) g = std::max(g, s / d);
+  }
+  return g;
+}
+
+// Dense inverse of the SPD matrix A (n <= a few thousand) by Cholesky
+// A = L L^T and n solves; false when a pivot is not positive.
+static bool spd_inverse(const HCSR& A, std::vector<double>& inv) {
+  const int64_t n = A.nrows;
+  std::vector<double> L(size_t(n) * n, 0.0);  // row-major lower triangle
+  for (int64_t r = 0; r < n; ++r)
+    for (int32_t k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k)
+      if (A.col[k] <= r) L[size_t(r) * n + A.col[k]] = A.val[k];
+  for (int64_t j = 0; j < n; ++j) {
+    double d = L[size_t(j) * n + j];
+    for (int64_t k = 0; k < j; ++k) d -= L[size_t(j) * n + k] * L[size_t(j) * n + k];
+    if (!(d > 0)) return false;
+    d = std::sqrt(d);
+    L[size_t(j) * n + j] = d;
+    for (int64_t i = j + 1; i < n; ++i) {
+      double t = L[size_t(i) * n + j];
+      for (int64_t k = 0; k < j; ++k) t -= L[size_t(i) * n + k] * L[size_t(j) * n + k];
+      L[size_t(i) * n + j] = t / d;
+    }
+  }
+  inv.assign(size_t(n) * n, 0.0);
+  std::vector<double> y(n);
+  for (int64_t c = 0; c < n; ++c) {  // column c of A^{-1}: L y = e_c, L^T x = y
+    for (int64_t i = 0; i < n; ++i) {
+      double t = (i == c) ? 1.0 : 0.0;
+      for (int64_t k = 0; k < i; ++k) t -= L[size_t(i) * n + k] * y[k];
+      y[i] = t / L[size_t(i) * n + i];
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {
+      double t = y[i];
+      for (int64_t k = i + 1; k < n; ++k) t -= L[size_t(k) * n + i] * inv[size_t(c) * n + k];
+      inv[size_t(c) * n + i] = t / L[size_t(i) * n + i];
+    }
+  }
+  return true;
 }
 
 static void free_csr(DCSR& D) {
@@ -213,6 +319,35 @@ int upload_levels(mmd_handle* h) {
     if ((rc = dput(&L.d_perm, perm[k]))) return rc;
     if ((rc = dput(&L.d_iperm, iperm[k]))) return rc;
   }
+  // V-cycle preconditioner of the level-0 refinement solves: Psi^T per level,
+  // 1 / diag and the Gershgorin bound per smoothed level, the coarsest inverse
+  h->mg_ok = false;
+  const int64_t nK = h->dl[K].n;
+  if (K >= 1 && nK <= kMgMaxCoarse) {
+    std::vector<double> inv;
+    const HCSR& AK = h->levels[K - 1].A;
+    if (spd_inverse(AK, inv)) {
+      for (int k = 0; k < K; ++k) {
+        DLevel& L = h->dl[k];
+        const HCSR& A = (k == 0) ? h->A0 : h->levels[k - 1].A;
+        L.gersh = gershgorin(A);
+        std::vector<float> dinv(A.nrows);
+        for (int64_t i = 0; i < A.nrows; ++i) {  // device order
+          const int32_t r = perm[k][i];
+          double d = 0;
+          for (int32_t e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e)
+            if (A.col[e] == r) d = A.val[e];
+          dinv[i] = (float)(1.0 / d);
+        }
+        if ((rc = dput(&L.dinv32, dinv))) return rc;
+        const HLevel& H = h->levels[k];
+        if ((rc = upload_csr(transpose(permute_rect(H.psi, perm[k], iperm[k + 1])), h->dl[k + 1].psiT))) return rc;
+      }
+      std::vector<float> kinv(inv.begin(), inv.end());  // natural order = device order on level K
+      if ((rc = dput(&h->dl[K].kinv32, kinv))) return rc;
+      h->mg_ok = true;
+    }
+  }
   return MMD_OK;
 }
 
@@ -221,6 +356,9 @@ void free_device(mmd_handle* h) {
     free_csr(L.A);
     free_csr(L.M);
     free_csr(L.psi);
+    free_csr(L.psiT);
+    cudaFree(L.dinv32);
+    cudaFree(L.kinv32);
     cudaFree(L.seg_ptr);
     cudaFree(L.phi_next);
     cudaFree(L.d_perm);
@@ -268,6 +406,7 @@ void mmd_default_eig_opts(mmd_eig_opts* o) {
   o->profile = 0;
   o->method = MMD_HIERARCHICAL;
   o->stop_level = 0;
+  o->mg_refine = 2;
 }
 
 int mmd_build(const mmd_csr* A, const mmd_build_opts* opts, mmd_handle** out) {
@@ -431,6 +570,30 @@ int mmd_level_op_block(mmd_handle* h, int k, int m, const double* X, double* Y, 
   return level_op_block(h, k, m, X, Y, tol, max_iter, iters, precision, (cudaStream_t)stream);
 }
 
+int mmd_spmv_tuning(const mmd_handle* h, int k, int which, float* ms_per_variant) {
+  if (!h || !h->on_device || k < 0 || k > (int)h->levels.size() || (which != 0 && which != 1) ||
+      (which == 1 && k == 0)) {
+    set_error("mmd_spmv_tuning: bad arguments");
+    return MMD_EINVAL;
+  }
+  const DCSR& D = which ? h->dl[k].M : h->dl[k].A;
+  if (ms_per_variant)
+    for (size_t v = 0; v < D.spmv_ms.size(); ++v) ms_per_variant[v] = D.spmv_ms[v];
+  return D.spmv_variant;
+}
+
+int mmd_level_vcycle(mmd_handle* h, int m, const double* R, double* Z, int deg, void* stream) {
+  if (!h || !h->on_device || m < 1 || !R || !Z || deg < 1 || deg > 8) {
+    set_error("mmd_level_vcycle: bad arguments");
+    return MMD_EINVAL;
+  }
+  if (!h->mg_ok) {
+    set_error("mmd_level_vcycle: the handle has no V-cycle (no coarse level, or a coarsest level above 2048 rows)");
+    return MMD_EINVAL;
+  }
+  return level_vcycle(h, m, R, Z, deg, (cudaStream_t)stream);
+}
+
 int mmd_level_bsolve(mmd_handle* h, int k, const double* q, double* x, double tol, int max_iter, int64_t* iters,
                      void* stream) {
   if (!h || !h->on_device || k < 1 || k > (int)h->levels.size() || !q || !x || !(tol > 0) || max_iter < 1) {
@@ -460,6 +623,7 @@ static bool validated_opts(const mmd_eig_opts* opts, const char* who, mmd_eig_op
     bad = "method must be MMD_HIERARCHICAL or MMD_IRLM_CG";
   else if (o.stop_level < 0 || o.stop_level > 16) bad = "stop_level must be in [0, K]";
   else if (o.method == MMD_IRLM_CG && o.stop_level != 0) bad = "stop_level applies to MMD_HIERARCHICAL only";
+  else if (o.mg_refine < 0 || o.mg_refine > 8) bad = "mg_refine must be in [0, 8]";
   if (!bad.empty()) {
     set_error(std::string(who) + ": invalid options: " + bad);
     return false;

@@ -84,6 +84,68 @@ __global__ void spmv_kernel(Sell A, const double* __restrict__ x, int64_t ldx, d
   }
 }
 
+// y = A x for one column, SELL-32, one row per lane: chunks of U entries
+// whose value and column loads, then gathers, are in flight together (the
+// last chunk cut by a warp-uniform predicate, len being the slice's); the
+// matrix is streamed once (evict-first loads), x is gathered through the
+// cache.  BS threads per block, at least MINB blocks per SM (bounds the
+// registers so that enough warps are resident to cover the memory latency).
+template <int U, int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB)
+    spmv1_kernel(Sell A, const double* __restrict__ x, double* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t(blockIdx.x) * BS + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * BS) >> 5;
+  for (int64_t sl = gw; sl < A.nslices; sl += nw) {
+    const int32_t base = A.ptr[sl] + lane, len = A.len[sl];
+    const int32_t row = A.row[sl * 32 + lane];
+    double acc = 0.0;
+    for (int32_t k = 0; k < len; k += U) {
+      double a[U];
+      int32_t j[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (k + u < len) {
+          a[u] = __ldcs(A.val + base + (k + u) * 32);
+          j[u] = __ldcs(A.col + base + (k + u) * 32);
+        } else {
+          a[u] = 0.0;
+          j[u] = 0;
+        }
+      }
+      double xv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) xv[u] = (k + u < len) ? __ldg(x + j[u]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (k + u < len) acc = fma(a[u], xv[u], acc);
+    }
+    if (row >= 0) y[row] = acc;
+  }
+}
+
+struct Spmv1Variant {
+  void (*fn)(Sell, const double*, double*);
+  int bs, minb;
+};
+const Spmv1Variant kSpmv1[] = {
+    {spmv1_kernel<4, 128, 10>, 128, 10}, {spmv1_kernel<4, 256, 5>, 256, 5},  {spmv1_kernel<8, 128, 8>, 128, 8},
+    {spmv1_kernel<8, 256, 4>, 256, 4},   {spmv1_kernel<8, 512, 2>, 512, 2},  {spmv1_kernel<16, 128, 4>, 128, 4},
+};
+constexpr int kNumSpmv1 = int(sizeof(kSpmv1) / sizeof(kSpmv1[0]));
+
+void launch_spmv1(int v, const Sell& A, const double* x, double* y, cudaStream_t st) {
+  const Spmv1Variant& K = kSpmv1[v];
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int64_t blocks = (A.nslices * 32 + K.bs - 1) / K.bs;
+  const int64_t cap = int64_t(nsm) * K.minb * 4;  // a few waves of resident blocks, then a slice-stride loop
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  K.fn<<<(int)blocks, K.bs, 0, st>>>(A, x, y);
+}
+
 constexpr int kDotBlocks = 512;
 
 __global__ void dots_stage1(const double* x, const double* y, int64_t n, int64_t ld, int m, double* part) {
@@ -386,11 +448,49 @@ void k_axpy(double* y, const double* x, int64_t n, double a, cudaStream_t st) {
 }
 
 void k_spmv(const Sell& A, const double* x, int64_t ldx, double* y, int64_t ldy, int m, cudaStream_t st) {
+  if (m == 1 && A.variant >= 0 && A.variant < kNumSpmv1) {
+    launch_spmv1(A.variant, A, x, y, st);
+    return;
+  }
   const int threads = 256;
   int64_t blocks = (A.nslices * 32 + threads - 1) / threads;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks < 1) blocks = 1;
   spmv_kernel<<<(int)blocks, threads, 0, st>>>(A, x, ldx, y, ldy, m);
+}
+
+int k_spmv_variants() { return kNumSpmv1; }
+
+int k_spmv_autotune(const Sell& A, const double* x, double* y, cudaStream_t st, float* ms_out) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return -1;
+  }
+  int best = -1;
+  float best_ms = 0.f;
+  for (int v = 0; v < kNumSpmv1; ++v) {
+    launch_spmv1(v, A, x, y, st);  // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 5; ++r) launch_spmv1(v, A, x, y, st);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      best = -1;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= 5.f;
+    if (ms_out) ms_out[v] = ms;
+    if (best < 0 || ms < best_ms) {
+      best = v;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
 }
 
 void k_dots(const double* x, const double* y, int64_t n, int64_t ld, int m, double* out, double* scratch,

@@ -135,7 +135,34 @@ Sell sell_of(const DCSR& A) {
   s.col = A.s_col;
   s.val = A.s_val;
   s.val32 = A.s_val32;
+  s.variant = A.spmv_variant;
   return s;
+}
+
+// CSR view for the V-cycle, with the lanes per row g that minimise the
+// dependent load rounds a block runs on a grid of `blocks` 1024-thread blocks:
+// SELL (g = 0, one row per lane): ceil(slices per block / 32 warps) x
+// ceil(row length / 2); CSR with g lanes per row: ceil(rows per block /
+// (1024 / g) groups) x (1 + ceil(row length / g)).  Long rows on few rows (the
+// coarse Galerkin matrices, Psi^T) share a row; level 0 keeps one row per lane.
+Csr32 csr32_of(const DCSR& A, int blocks) {
+  Csr32 c;
+  c.rowptr = A.rowptr;
+  c.col = A.col;
+  c.val = A.val32;
+  c.nrows = A.nrows;
+  const double L = std::max(1.0, A.mean_row), B = std::max(1, blocks);
+  const double rows_blk = std::ceil(double(A.nrows) / B), slices_blk = std::ceil(double(A.nslices) / B);
+  double best = std::ceil(slices_blk / 32.0) * std::ceil(L / 2.0);
+  c.g = 0;
+  for (int g : {8, 32}) {
+    const double cost = std::ceil(rows_blk / (1024.0 / g)) * (1.0 + std::ceil(L / g));
+    if (cost < best) {
+      best = cost;
+      c.g = g;
+    }
+  }
+  return c;
 }
 
 // ------------------------------------------------------------ context
@@ -291,6 +318,59 @@ struct Ctx {
     if (!done && notconv) ++*notconv;
   }
 
+  // The V-cycle's level table (device memory) and work vectors, for tiles of
+  // up to four columns (level 0 of the handle; mode 3 of the solver).
+  void set_mg(SolverArgs& a, int deg, int only) {
+    const int K = (int)h->levels.size();
+    const int MTmax = 4;
+    std::vector<MGLevel> lv(K);
+    for (int k = 0; k < K; ++k) {
+      const DLevel& L = h->dl[k];
+      MGLevel& g = lv[k];
+      g.A = sell_of(L.A);
+      g.P = sell_of(h->dl[k + 1].psi);
+      g.PT = sell_of(h->dl[k + 1].psiT);
+      g.cA = csr32_of(L.A, ws->nsm);
+      g.cP = csr32_of(h->dl[k + 1].psi, ws->nsm);
+      g.cPT = csr32_of(h->dl[k + 1].psiT, ws->nsm);
+      g.dinv = L.dinv32;
+      g.hi = L.gersh;
+      // Chebyshev iteration on [hi / 30, hi]: theta, delta the interval's centre and
+      // half-width, sigma = theta / delta, rho_0 = 1 / sigma, rho_s = 1 / (2 sigma - rho_{s-1});
+      // step 0: d = D^{-1} res / theta; step s: d = rho_s rho_{s-1} d + (2 rho_s / delta) D^{-1} res
+      {
+        const double hi = L.gersh, lo = hi / 30.0, th = 0.5 * (hi + lo), de = 0.5 * (hi - lo), sg = th / de;
+        double rho = 1.0 / sg;
+        g.c1[0] = 0.f;
+        g.c2[0] = (float)(1.0 / th);
+        for (int st = 1; st < 8; ++st) {
+          const double rn = 1.0 / (2.0 * sg - rho);
+          g.c1[st] = (float)(rn * rho);
+          g.c2[st] = (float)(2.0 * rn / de);
+          rho = rn;
+        }
+      }
+      g.n = L.n;
+      const std::string t = std::to_string(k);
+      g.r = buf<float>(ws, "mg_r" + t, size_t(L.n) * MTmax);
+      g.x = buf<float>(ws, "mg_x" + t, size_t(L.n) * MTmax);
+      g.x2 = buf<float>(ws, "mg_y" + t, size_t(L.n) * MTmax);
+      g.d = buf<float>(ws, "mg_d" + t, size_t(L.n) * MTmax);
+    }
+    MGLevel* dlv = buf<MGLevel>(ws, "mg_levels", K);
+    CK(cudaMemcpyAsync(dlv, lv.data(), sizeof(MGLevel) * K, cudaMemcpyHostToDevice, st));
+    const int64_t nK = h->dl[K].n;
+    a.mg = dlv;
+    a.mg_K = K;
+    a.mg_deg = deg;
+    a.mg_kinv = h->dl[K].kinv32;
+    a.mg_rK = buf<float>(ws, "mg_rK", size_t(nK) * MTmax);
+    a.mg_xK = buf<float>(ws, "mg_xK", size_t(nK) * MTmax);
+    a.mg_nK = nK;
+    a.mg_only = only;
+  }
+  int mg_deg = 2, mg_only = 0;
+
   void solve_raw(int k, int mode, bool fp32, const void* B, void* X, int m, int x0, double tol, int maxit,
                  std::vector<int64_t>* iters, int64_t* inner_total, int* notconv, const double* B64 = nullptr,
                  double* X64 = nullptr, std::vector<int>* conv_out = nullptr) {
@@ -359,6 +439,7 @@ struct Ctx {
       a.bar.gen = ws->bar + 32;
       a.bar.status = ws->status;
       a.bar.timeout_ns = (long long)timeout_ns;
+      if (mode == 3) set_mg(a, mg_deg, mg_only);
       CK(cudaMemsetAsync(ws->in_out, 0, sizeof(int64_t), st));
       CK(cudaMemsetAsync(ws->bar, 0, sizeof(unsigned), st));
       if (o.profile) {
@@ -623,6 +704,10 @@ ExtendOut extend(Ctx& c, int k, double* BAS, int m0, int cap, const std::vector<
   ExtendOut out{m0, Dini};
   const int64_t n = c.h->dl[k].n;
   if (m0 >= m_tar || n - m0 <= 0) return out;
+  // no extension threshold (level 0, the last level computed): the searching
+  // step only serves the test of mu-hat against mu_ex (Section 6), so one
+  // extension goes straight to the target
+  if (!has_mu_ex && c.o.d == 0) d = std::max(1, m_tar - m0);
   double* f = buf<double>(c.ws, "ex_f", n);
   Lanczos lz(c, k, BAS, m0, cap, f, stream0 + 1);
   k_random(f, n, c.o.seed, stream0, c.h->dl[k].d_perm, c.st);
@@ -730,6 +815,7 @@ int refine(Ctx& c, int k, double* Q0, std::vector<double>& D, double tol_rel, do
            double delta_h, double* Qout) {
   const int m = (int)D.size();
   if (m == 0) return 0;
+  const auto t_start = std::chrono::steady_clock::now();
   const DLevel& L = c.h->dl[k];
   const int64_t n = L.n;
   double* R = buf<double>(c.ws, "rf_R", size_t(n) * m);
@@ -780,7 +866,14 @@ int refine(Ctx& c, int k, double* Q0, std::vector<double>& D, double tol_rel, do
       std::vector<int64_t> its;
       int64_t inner = 0;
       int nc = 0;
-      c.solve(k, k == 0 ? 0 : 1, W, F, m, 1, tol_rel, c.o.max_cg_iter, &its, &inner, &nc);
+      if (k == 0 && c.h->mg_ok && c.o.mg_refine > 0) {
+        // warm-started level-0 solves preconditioned by the decomposition (FP32 V-cycle, FP64 PCG)
+        c.mg_deg = c.o.mg_refine;
+        c.mg_only = 0;
+        c.solve_raw(0, 3, false, W, F, m, 1, tol_rel, c.o.max_cg_iter, &its, &inner, &nc);
+      } else {
+        c.solve(k, k == 0 ? 0 : 1, W, F, m, 1, tol_rel, c.o.max_cg_iter, &its, &inner, &nc);
+      }
       c.S.refine_pcg_calls += m;
       for (auto t : its) c.S.refine_pcg_iters += t;
       c.S.inner_iters += inner;
@@ -829,7 +922,11 @@ int refine(Ctx& c, int k, double* Q0, std::vector<double>& D, double tol_rel, do
   }
   CK(cudaMemcpyAsync(Qout, Q, sizeof(double) * size_t(n) * mh, cudaMemcpyDeviceToDevice, c.st));
   D.resize(mh);
-  if (debug_on()) fprintf(stderr, "[mmd] level %d refine m=%d mh=%d done=%d\n", k, m, mh, (int)done);
+  if (debug_on()) {
+    c.sync();
+    fprintf(stderr, "[mmd] level %d refine m=%d mh=%d done=%d time %.1f ms\n", k, m, mh, (int)done,
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count());
+  }
   return mh;
 }
 
@@ -994,6 +1091,30 @@ int level_op_block(mmd_handle* h, int k, int m, const double* x, double* y, doub
       set_error("mmd_level_op_block: PCG reached max_iter");
       return MMD_ENOCONV;
     }
+  } catch (const CudaFail& f) {
+    return f.code;
+  }
+  return MMD_OK;
+}
+
+int level_vcycle(mmd_handle* h, int m, const double* R, double* Z, int deg, cudaStream_t st) {
+  try {
+    mmd_eig_opts o;
+    mmd_default_eig_opts(&o);
+    Ctx c(h, st, o);
+    CK(cudaMemsetAsync(c.ws->status, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(c.ws->bar, 0, 2 * sizeof(unsigned), st));
+    const DLevel& L = h->dl[0];
+    double* a = buf<double>(c.ws, "lv_a", size_t(L.n) * m);
+    double* b = buf<double>(c.ws, "lv_b", size_t(L.n) * m);
+    k_gather(R, L.n, L.d_perm, L.n, m, a, L.n, st);
+    c.mg_deg = deg;
+    c.mg_only = 1;
+    std::vector<int64_t> its;
+    c.solve_raw(0, 3, false, a, b, m, 0, 1e-30, 1, &its, nullptr, nullptr);
+    k_scatter(b, L.n, L.d_perm, L.n, m, Z, L.n, st);
+    c.sync();
+    CK(cudaGetLastError());
   } catch (const CudaFail& f) {
     return f.code;
   }

@@ -18,10 +18,37 @@ struct Sell {
   const int32_t* col = nullptr;
   const double* val = nullptr;
   const float* val32 = nullptr;
+  int variant = -1;  // single-column SpMV kernel picked by k_spmv_autotune (-1: not tuned)
+};
+
+// One level of the V-cycle preconditioner (FP32 work, device order of the
+// level): A^(k), Psi^(k+1) and its transpose, 1 / diag A^(k), the Gershgorin
+// bound of D^{-1} A^(k), and MT-interleaved work vectors.
+// CSR view (device order, FP32 values) of a V-cycle matrix whose rows are
+// long enough to share a row among g lanes (g = 0: use the SELL copy).
+struct Csr32 {
+  const int32_t* rowptr = nullptr;
+  const int32_t* col = nullptr;
+  const float* val = nullptr;
+  int64_t nrows = 0;
+  int g = 0;
+};
+
+struct MGLevel {
+  Sell A;               // A^(k) (val32 used)
+  Sell P;               // Psi^(k+1): rows of level k, columns of level k + 1
+  Sell PT;              // Psi^(k+1)^T: rows of level k + 1, columns of level k
+  Csr32 cA, cP, cPT;    // the same matrices as CSR, used when their g > 0
+  const float* dinv;    // n
+  double hi;            // upper end of the Chebyshev interval
+  // Chebyshev step st (pre- and post-smoothing alike): d = c1[st] d + c2[st] D^{-1} (r - A x), x += d
+  float c1[8], c2[8];
+  int64_t n;            // N^(k)
+  float *r, *x, *x2, *d;  // n x MT each: right-hand side, iterate (ping-pong), direction / residual
 };
 
 struct SolverArgs {
-  int mode;  // 0 CG, 1 flexible PCG with inner CG on M, 2 CG on P A P
+  int mode;  // 0 CG, 1 flexible PCG with inner CG on M, 2 CG on P A P, 3 flexible PCG with the V-cycle
   int64_t n;
   Sell A;
   Sell M;
@@ -47,6 +74,13 @@ struct SolverArgs {
   int64_t* in_out;     // [1], accumulated
   int* conv;           // [m]
   GridBarrier bar;
+  // mode 3: the V-cycle (levels 0 .. mg_K - 1 in device memory, dense coarsest inverse)
+  const MGLevel* mg;
+  int mg_K, mg_deg;
+  const float* mg_kinv;  // nK x nK, column-major
+  float *mg_rK, *mg_xK;  // nK x MT
+  int64_t mg_nK;
+  int mg_only;  // 1: apply z = V(b) once (x = z, column-major) instead of solving
 };
 
 int solver_threads(int mt);
@@ -58,8 +92,15 @@ void k_fill(double* x, int64_t n, double v, cudaStream_t st);
 void k_copy(double* y, const double* x, int64_t n, cudaStream_t st);
 void k_scal(double* x, int64_t n, double a, cudaStream_t st);
 void k_axpy(double* y, const double* x, int64_t n, double a, cudaStream_t st);
-// y = A x (SELL-32), columns m of ld (x, y column-major)
+// y = A x (SELL-32), columns m of ld (x, y column-major); one column runs the
+// single-column variant in A.variant when it has been tuned
 void k_spmv(const Sell& A, const double* x, int64_t ldx, double* y, int64_t ldy, int m, cudaStream_t st);
+// Times every single-column SpMV variant on A (x, y: scratch vectors of A's
+// size) with events on st and returns the fastest one's index; ms_out (may be
+// NULL) receives each variant's mean time.  Variants differ in the entries
+// in flight per lane, the block size and the register bound.
+int k_spmv_autotune(const Sell& A, const double* x, double* y, cudaStream_t st, float* ms_out);
+int k_spmv_variants();
 // dot products: out[c] = sum_i x(i,c) y(i,c), deterministic two-stage; scratch >= 1024*m doubles
 void k_dots(const double* x, const double* y, int64_t n, int64_t ld, int m, double* out, double* scratch,
             cudaStream_t st);

@@ -45,6 +45,8 @@ struct DCSR {
   int32_t* s_col = nullptr;   // sell_nnz
   double* s_val = nullptr;    // sell_nnz
   float* s_val32 = nullptr;   // sell_nnz
+  int spmv_variant = -1;      // single-column SpMV kernel chosen by the autotuner at upload
+  std::vector<float> spmv_ms; // its timing of every variant (ms)
 };
 
 // Device level data.  Level k's vectors are stored in "device order": the
@@ -64,6 +66,11 @@ struct DLevel {
   int32_t* d_perm = nullptr;   // same on device
   int32_t* d_iperm = nullptr;  // natural index -> device position
   double eps = 0, delta = 0;   // of P^(k) (k >= 1)
+  // V-cycle preconditioner data (present when the handle's mg_ok is set)
+  DCSR psiT;                   // (Psi^(k))^T: level k (rows) x level k-1 (cols), k >= 1
+  float* dinv32 = nullptr;     // 1 / diag A^(k), k < K
+  double gersh = 0;            // max_i sum_j |a_ij| / a_ii of A^(k), k < K
+  float* kinv32 = nullptr;     // k = K: (A^(K))^{-1}, dense N^(K) x N^(K)
 };
 
 struct Workspace;
@@ -85,6 +92,7 @@ struct mmd_handle {
   int last_N = 0;
   int32_t* d_in_rowptr = nullptr;  // input CSR pattern (natural order), uploaded by eig_grad
   int32_t* d_in_col = nullptr;
+  bool mg_ok = false;  // V-cycle data uploaded (K >= 1 and a dense-invertible coarsest level)
 };
 
 namespace mmd {

@@ -327,6 +327,241 @@ __device__ bool inner_cg(const SolverArgs& a, Sh<MT>& s) {
   return true;
 }
 
+// ---- mode 3: the V-cycle preconditioner z = V(r), FP32 work
+//
+// Section 2.3's representation A^{-1} = U B^{-1} U^T + Psi (Psi^T A Psi)^{-1}
+// Psi^T (and its K-level form) applied as a symmetric V-cycle over the
+// decomposition's levels: on level k a Chebyshev smoother of D^{-1} A^(k)
+// (the fine-scale part; interval [hi / 30, hi], hi the Gershgorin bound),
+// restriction by Psi^(k+1)^T, the same cycle on level k + 1, prolongation by
+// Psi^(k+1), the same smoother again; the coarsest level by its dense
+// inverse.  Every step is one pass over a level's rows followed by a grid
+// barrier; vectors are MT-interleaved FP32, the outer iteration stays FP64.
+
+// per_row(row, acc) for every row of the SELL matrix A, acc = A(row, :) X
+template <int MT, typename F>
+__device__ __forceinline__ void mg_rows(const Sell& A, const float* __restrict__ X, F&& per_row) {
+  const int lane = threadIdx.x & 31;
+  FOR_BLOCK_SLICES(sl, A.nslices) {
+    const int32_t base = A.ptr[sl] + lane, len = A.len[sl];
+    const int32_t row = A.row[sl * 32 + lane];
+    float acc[MT];
+#pragma unroll
+    for (int c = 0; c < MT; ++c) acc[c] = 0.f;
+    int32_t k = 0;
+    for (; k + 2 <= len; k += 2) {
+      const float a0 = A.val32[base + k * 32], a1 = A.val32[base + (k + 1) * 32];
+      const int64_t j0 = A.col[base + k * 32], j1 = A.col[base + (k + 1) * 32];
+      float x0[MT], x1[MT];
+      load_row<MT, float>(X, j0, x0);
+      load_row<MT, float>(X, j1, x1);
+#pragma unroll
+      for (int c = 0; c < MT; ++c) acc[c] = fmaf(a1, x1[c], fmaf(a0, x0[c], acc[c]));
+    }
+    if (k < len) {
+      const float a0 = A.val32[base + k * 32];
+      const int64_t j0 = A.col[base + k * 32];
+      float x0[MT];
+      load_row<MT, float>(X, j0, x0);
+#pragma unroll
+      for (int c = 0; c < MT; ++c) acc[c] = fmaf(a0, x0[c], acc[c]);
+    }
+    if (row >= 0) per_row(row, acc);
+  }
+}
+
+// The same for a CSR matrix with g lanes per row (long rows of the coarse
+// Galerkin matrices and of Psi^T): the group's lanes load consecutive
+// entries, then add their partial sums by shuffles; the group's first lane
+// calls per_row.  Rows are split into one contiguous share per block.
+template <int MT, int G, typename F>
+__device__ __forceinline__ void mg_rows_csr_g(const Csr32& A, const float* __restrict__ X, F&& per_row) {
+  const int sub = threadIdx.x & (G - 1);
+  const int64_t lo = share_lo(A.nrows), hi = share_hi(A.nrows);
+  const int ngrp = blockDim.x / G;
+  // every lane of a group runs the same number of rounds (the shuffles need the whole group)
+  for (int64_t r0 = lo; r0 < hi; r0 += ngrp) {
+    const int64_t row = r0 + threadIdx.x / G;
+    float acc[MT];
+#pragma unroll
+    for (int c = 0; c < MT; ++c) acc[c] = 0.f;
+    if (row < hi) {
+      const int32_t e0 = A.rowptr[row], e1 = A.rowptr[row + 1];
+      for (int32_t e = e0 + sub; e < e1; e += G) {
+        const float a = A.val[e];
+        float xv[MT];
+        load_row<MT, float>(X, A.col[e], xv);
+#pragma unroll
+        for (int c = 0; c < MT; ++c) acc[c] = fmaf(a, xv[c], acc[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < MT; ++c)
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o, G);
+    if (row < hi && sub == 0) per_row((int32_t)row, acc);
+  }
+}
+
+// per_row over a V-cycle matrix: CSR with g lanes per row when its rows are
+// long, else the SELL copy with one row per lane
+template <int MT, typename F>
+__device__ __forceinline__ void mg_apply(const Sell& S, const Csr32& C, const float* __restrict__ X, F&& per_row) {
+  if (C.g == 32)
+    mg_rows_csr_g<MT, 32>(C, X, per_row);
+  else if (C.g == 8)
+    mg_rows_csr_g<MT, 8>(C, X, per_row);
+  else
+    mg_rows<MT>(S, X, per_row);
+}
+
+// The buffer holding level k's iterate after its pre-smoothing (deg - 1
+// ping-pong swaps) and after its post-smoothing (deg more).
+__device__ __forceinline__ float* mg_xpre(const MGLevel& L, int deg) { return ((deg - 1) & 1) ? L.x2 : L.x; }
+__device__ __forceinline__ float* mg_xpost(const MGLevel& L, int deg) {
+  return ((2 * deg - 1) & 1) ? L.x2 : L.x;
+}
+
+// z = V(r) for the columns with act[c] (r, z: the outer solver's FP64
+// interleaved vectors); the other columns' z is left alone.
+template <int MT>
+__device__ __forceinline__ bool mg_vcycle(const SolverArgs& a, const int* act) {
+  const double* __restrict__ r0 = (const double*)a.r;
+  double* __restrict__ z0 = (double*)a.z;
+  const int K = a.mg_K, deg = a.mg_deg;
+  int on[MT];
+#pragma unroll
+  for (int c = 0; c < MT; ++c) on[c] = (c < a.m) && act[c];
+  // ---- down: pre-smoothing from x = 0, residual, restriction
+  for (int k = 0; k < K; ++k) {
+    const MGLevel& L = a.mg[k];
+    float* x = L.x;
+    float* x2 = L.x2;
+    float* __restrict__ rr = L.r;
+    float* __restrict__ dd = L.d;
+    const float* __restrict__ dinv = L.dinv;
+    const float c0 = L.c2[0];
+    FOR_BLOCK_SHARE(i, L.n)
+      _Pragma("unroll") for (int c = 0; c < MT; ++c) {
+        const int64_t o = wix<MT>(i, c);
+        float rv;
+        if (k == 0) {
+          rv = on[c] ? (float)r0[o] : 0.f;
+          rr[o] = rv;
+        } else {
+          rv = rr[o];
+        }
+        const float dv = c0 * dinv[i] * rv;
+        dd[o] = dv;
+        x[o] = dv;
+      }
+    if (!grid_sync(a.bar)) return false;
+    for (int st = 1; st < deg; ++st) {
+      const float c1 = L.c1[st], c2 = L.c2[st];
+      const float* xs = x;
+      float* xd = x2;
+      mg_apply<MT>(L.A, L.cA, xs, [&](int32_t row, const float* acc) {
+#pragma unroll
+        for (int c = 0; c < MT; ++c) {
+          const int64_t o = wix<MT>(row, c);
+          const float dv = fmaf(c1, dd[o], c2 * dinv[row] * (rr[o] - acc[c]));
+          dd[o] = dv;
+          xd[o] = xs[o] + dv;
+        }
+      });
+      if (!grid_sync(a.bar)) return false;
+      float* t = x;
+      x = x2;
+      x2 = t;
+    }
+    // residual of the pre-smoothed iterate (into d), then its restriction
+    {
+      const float* xs = x;
+      mg_apply<MT>(L.A, L.cA, xs, [&](int32_t row, const float* acc) {
+#pragma unroll
+        for (int c = 0; c < MT; ++c) {
+          const int64_t o = wix<MT>(row, c);
+          dd[o] = rr[o] - acc[c];
+        }
+      });
+    }
+    if (!grid_sync(a.bar)) return false;
+    float* __restrict__ rnext = (k + 1 < K) ? a.mg[k + 1].r : a.mg_rK;
+    mg_apply<MT>(L.PT, L.cPT, dd, [&](int32_t row, const float* acc) {
+#pragma unroll
+      for (int c = 0; c < MT; ++c) rnext[wix<MT>(row, c)] = acc[c];
+    });
+    if (!grid_sync(a.bar)) return false;
+  }
+  // ---- coarsest: x_K = A_K^{-1} r_K (symmetric inverse, row i read as column i), one warp per row
+  {
+    const int64_t nK = a.mg_nK;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t row = warp; row < nK; row += nw) {
+      float acc[MT];
+#pragma unroll
+      for (int c = 0; c < MT; ++c) acc[c] = 0.f;
+      for (int64_t j = lane; j < nK; j += 32) {
+        const float kv = a.mg_kinv[j + row * nK];
+        float xv[MT];
+        load_row<MT, float>(a.mg_rK, j, xv);
+#pragma unroll
+        for (int c = 0; c < MT; ++c) acc[c] = fmaf(kv, xv[c], acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < MT; ++c) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+        if (lane == 0) a.mg_xK[wix<MT>(row, c)] = acc[c];
+      }
+    }
+    if (!grid_sync(a.bar)) return false;
+  }
+  // ---- up: prolongation, post-smoothing
+  for (int k = K - 1; k >= 0; --k) {
+    const MGLevel& L = a.mg[k];
+    float* x = mg_xpre(L, deg);
+    float* x2 = (x == L.x) ? L.x2 : L.x;
+    float* __restrict__ rr = L.r;
+    float* __restrict__ dd = L.d;
+    const float* __restrict__ dinv = L.dinv;
+    const float* __restrict__ xc = (k + 1 < K) ? mg_xpost(a.mg[k + 1], deg) : a.mg_xK;
+    {
+      float* xw = x;
+      mg_apply<MT>(L.P, L.cP, xc, [&](int32_t row, const float* acc) {
+#pragma unroll
+        for (int c = 0; c < MT; ++c) xw[wix<MT>(row, c)] += acc[c];
+      });
+    }
+    if (!grid_sync(a.bar)) return false;
+    for (int st = 0; st < deg; ++st) {
+      const float c1 = L.c1[st], c2 = L.c2[st];
+      const bool out = (k == 0) && (st == deg - 1);
+      const float* xs = x;
+      float* xd = x2;
+      mg_apply<MT>(L.A, L.cA, xs, [&](int32_t row, const float* acc) {
+#pragma unroll
+        for (int c = 0; c < MT; ++c) {
+          const int64_t o = wix<MT>(row, c);
+          const float g = c2 * dinv[row] * (rr[o] - acc[c]);
+          const float dv = (st == 0) ? g : fmaf(c1, dd[o], g);
+          dd[o] = dv;
+          const float xn = xs[o] + dv;
+          xd[o] = xn;
+          if (out && on[c]) z0[o] = (double)xn;
+        }
+      });
+      if (!grid_sync(a.bar)) return false;
+      float* t = x;
+      x = x2;
+      x2 = t;
+    }
+  }
+  return true;
+}
+
 // Mode 0: CG in the Chronopoulos-Gear form: r^T r and r^T A r are both
 // formed in the SpMV pass (w = A r), so an iteration has one reduction round
 // (block sums, grid barrier, partials) and one plain grid barrier before the
@@ -589,7 +824,9 @@ __device__ bool cg_rel(const SolverArgs& a, Sh<MT>& s) {
   return true;
 }
 
-template <int MT, typename T>
+// VC = 1: the instance with the V-cycle preconditioner (mode 3), kept apart
+// so that the other modes' register allocation does not see the call.
+template <int MT, typename T, int VC>
 __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs a) {
   __shared__ Sh<MT> s;
   grid_sync_init();
@@ -601,6 +838,23 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
   T* const z = (T*)a.z;
   const int m = a.m;
   const int64_t n = a.n, ld = a.ld;
+  if constexpr (VC == 1 && sizeof(T) == 8) {
+    if (a.mg_only) {  // one application z = V(b): b and x column-major, all m columns
+      FOR_BLOCK_SHARE(i, n)
+        _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) r[wix<MT>(i, c)] = b[i + c * ld];
+      if (threadIdx.x < MT) s.act[threadIdx.x] = threadIdx.x < m;
+      __syncthreads();
+      if (!grid_sync(a.bar)) return;
+      if (!mg_vcycle<MT>(a, s.act)) return;
+      FOR_BLOCK_SHARE(i, n)
+        _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) x[i + c * ld] = z[wix<MT>(i, c)];
+      if (blockIdx.x == 0 && threadIdx.x < m) {
+        a.it_out[threadIdx.x] = 1;
+        a.conv[threadIdx.x] = 1;
+      }
+      return;
+    }
+  }
   if (a.mode == 0 && a.b64) {
     if (!cg_rel<MT, T>(a, s)) return;
     if (blockIdx.x == 0 && threadIdx.x < m) {
@@ -680,8 +934,12 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
     return;
   }
   T* zv = r;
-  if (a.mode == 1) {
-    if (!inner_cg<MT, T>(a, s)) return;
+  if (a.mode == 1 || a.mode == 3) {
+    if (a.mode == 1) {
+      if (!inner_cg<MT, T>(a, s)) return;
+    } else if constexpr (sizeof(T) == 8 && VC == 1) {
+      if (!mg_vcycle<MT>(a, s.act)) return;
+    }
     zv = z;
 #pragma unroll
     for (int c = 0; c < MT; ++c) acc[c] = T(0);
@@ -768,7 +1026,7 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
       }
     }
     __syncthreads();
-    if (a.mode == 1) {
+    if (a.mode == 1 || a.mode == 3) {
       // columns that just converged (-1) need no preconditioning
       if (threadIdx.x < m) {
         const int c = threadIdx.x;
@@ -776,7 +1034,11 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
         s.rr[c] = s.val2[c];
       }
       __syncthreads();
-      if (!inner_cg<MT, T>(a, s)) return;
+      if (a.mode == 1) {
+        if (!inner_cg<MT, T>(a, s)) return;
+      } else if constexpr (sizeof(T) == 8 && VC == 1) {
+        if (!mg_vcycle<MT>(a, s.act)) return;
+      }
 #pragma unroll
       for (int c = 0; c < MT; ++c) acc[c] = acc2[c] = T(0);
       FOR_BLOCK_SHARE(i, n)
@@ -830,28 +1092,29 @@ constexpr size_t dyn_smem() {
 }
 
 // the 64 KB of the four-column instance exceed the default 48 KB window
-template <int MT, typename T>
+template <int MT, typename T, int VC>
 void allow_smem() {
   static std::once_flag once;
   std::call_once(once, [] {
-    cudaFuncSetAttribute(solve_kernel<MT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem<MT>());
+    cudaFuncSetAttribute(solve_kernel<MT, T, VC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)dyn_smem<MT>());
   });
 }
 
-template <int MT, typename T>
+template <int MT, typename T, int VC>
 int max_blocks_for() {
-  allow_smem<MT, T>();
+  allow_smem<MT, T, VC>();
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<MT, T>, threads_for<MT>(), dyn_smem<MT>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<MT, T, VC>, threads_for<MT>(), dyn_smem<MT>());
   return nb;
 }
 
-template <int MT, typename T>
+template <int MT, typename T, int VC>
 cudaError_t launch_tpl(const SolverArgs& a, int grid, cudaStream_t st) {
-  allow_smem<MT, T>();
+  allow_smem<MT, T, VC>();
   void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel((const void*)solve_kernel<MT, T>, dim3(grid), dim3(threads_for<MT>()), args,
-                                     dyn_smem<MT>(), st);
+  return cudaLaunchCooperativeKernel((const void*)solve_kernel<MT, T, VC>, dim3(grid), dim3(threads_for<MT>()),
+                                     args, dyn_smem<MT>(), st);
 }
 
 }  // namespace
@@ -860,19 +1123,25 @@ int solver_threads(int mt) { return mt == 1 ? threads_for<1>() : threads_for<4>(
 
 // One block per SM (the reductions read one partial per block, <= 1024).
 int solver_max_grid(int mt, int num_sms) {
-  const int nb = (mt == 1) ? std::min(max_blocks_for<1, double>(), max_blocks_for<1, float>())
-                           : std::min(max_blocks_for<4, double>(), max_blocks_for<4, float>());
+  const int nb = (mt == 1) ? std::min(std::min(max_blocks_for<1, double, 0>(), max_blocks_for<1, float, 0>()),
+                                     max_blocks_for<1, double, 1>())
+                           : std::min(std::min(max_blocks_for<4, double, 0>(), max_blocks_for<4, float, 0>()),
+                                      max_blocks_for<4, double, 1>());
   const int g = (nb >= 1) ? num_sms : 0;
   return g > kMaxThreads ? kMaxThreads : g;
 }
 
 cudaError_t launch_solver(const SolverArgs& a, int mt, int grid, cudaStream_t st) {
-  if (a.fp32) {
-    if (mt == 1) return launch_tpl<1, float>(a, grid, st);
-    if (mt == 4) return launch_tpl<4, float>(a, grid, st);
+  if (a.mode == 3) {  // V-cycle: FP64 outer iteration only
+    if (a.fp32 || !a.mg || a.mg_K < 1) return cudaErrorInvalidValue;
+    if (mt == 1) return launch_tpl<1, double, 1>(a, grid, st);
+    if (mt == 4) return launch_tpl<4, double, 1>(a, grid, st);
+  } else if (a.fp32) {
+    if (mt == 1) return launch_tpl<1, float, 0>(a, grid, st);
+    if (mt == 4) return launch_tpl<4, float, 0>(a, grid, st);
   } else {
-    if (mt == 1) return launch_tpl<1, double>(a, grid, st);
-    if (mt == 4) return launch_tpl<4, double>(a, grid, st);
+    if (mt == 1) return launch_tpl<1, double, 0>(a, grid, st);
+    if (mt == 4) return launch_tpl<4, double, 0>(a, grid, st);
   }
   return cudaErrorInvalidValue;
 }
