@@ -68,8 +68,14 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& b) {
     while (ld_acquire(b.count) < target) {
       __nanosleep(20);
       if (((++spins) & 255u) == 1u) {  // first poll, then every 256th
-        if (ld_acquire_int(b.status) != DEV_OK || global_ns() - t0 > b.timeout_ns) {
-          atomicExch(b.status, (int)DEV_TIMEOUT);
+        // another block's status (not SPD, a timeout) ends the wait as it is;
+        // our own time limit turns an OK status into a timeout
+        if (ld_acquire_int(b.status) != DEV_OK) {
+          ok = 0;
+          break;
+        }
+        if (global_ns() - t0 > b.timeout_ns) {
+          atomicCAS(b.status, (int)DEV_OK, (int)DEV_TIMEOUT);
           ok = 0;
           break;
         }

@@ -57,7 +57,15 @@ struct Workspace {
   int64_t* it_out = nullptr;
   int64_t* in_out = nullptr;
   int* conv = nullptr;
+  // concurrent tiles of one multi-column solve: side streams and fork / join events
+  cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join[4] = {nullptr, nullptr, nullptr, nullptr};
   ~Workspace() {
+    for (int l = 0; l < 4; ++l) {
+      if (side[l]) cudaStreamDestroy(side[l]);
+      if (join[l]) cudaEventDestroy(join[l]);
+    }
+    if (fork) cudaEventDestroy(fork);
     for (auto& b : bufs) cudaFree(b.second.first);
     cudaFree(bar);
     cudaFree(status);
@@ -320,7 +328,7 @@ struct Ctx {
 
   // The V-cycle's level table (device memory) and work vectors, for tiles of
   // up to four columns (level 0 of the handle; mode 3 of the solver).
-  void set_mg(SolverArgs& a, int deg, int only) {
+  void set_mg(SolverArgs& a, int deg, int only, int lane = 0) {
     const int K = (int)h->levels.size();
     const int MTmax = 4;
     std::vector<MGLevel> lv(K);
@@ -351,25 +359,151 @@ struct Ctx {
         }
       }
       g.n = L.n;
-      const std::string t = std::to_string(k);
+      const std::string t = std::to_string(k) + "_" + std::to_string(lane);
       g.r = buf<float>(ws, "mg_r" + t, size_t(L.n) * MTmax);
       g.x = buf<float>(ws, "mg_x" + t, size_t(L.n) * MTmax);
       g.x2 = buf<float>(ws, "mg_y" + t, size_t(L.n) * MTmax);
       g.d = buf<float>(ws, "mg_d" + t, size_t(L.n) * MTmax);
     }
-    MGLevel* dlv = buf<MGLevel>(ws, "mg_levels", K);
+    MGLevel* dlv = buf<MGLevel>(ws, "mg_levels" + std::to_string(lane), K);
     CK(cudaMemcpyAsync(dlv, lv.data(), sizeof(MGLevel) * K, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));  // lv is a host stack array: complete the copy before it goes
     const int64_t nK = h->dl[K].n;
     a.mg = dlv;
     a.mg_K = K;
     a.mg_deg = deg;
     a.mg_kinv = h->dl[K].kinv32;
-    a.mg_rK = buf<float>(ws, "mg_rK", size_t(nK) * MTmax);
-    a.mg_xK = buf<float>(ws, "mg_xK", size_t(nK) * MTmax);
+    a.mg_rK = buf<float>(ws, "mg_rK" + std::to_string(lane), size_t(nK) * MTmax);
+    a.mg_xK = buf<float>(ws, "mg_xK" + std::to_string(lane), size_t(nK) * MTmax);
     a.mg_nK = nK;
     a.mg_only = only;
   }
   int mg_deg = 2, mg_only = 0;
+
+  // Tiles of MT columns distributed round-robin over `lanes` side streams,
+  // each lane with its own vectors, reduction partials, barrier counter and
+  // result slots; the caller's stream forks to and joins the lanes by events.
+  void solve_lanes(int k, int mode, bool fp32, const void* B, void* X, int m, int x0, double tol, int maxit,
+                   std::vector<int64_t>* iters, int64_t* inner_total, int* notconv, const double* B64, double* X64,
+                   std::vector<int>* conv_out, int MT, int grid, int lanes) {
+    const DLevel& L = h->dl[k];
+    const int64_t n = L.n;
+    const size_t eb = fp32 ? sizeof(float) : sizeof(double);
+    const std::string pre = fp32 ? "sv32_" : "sv_";
+    if (!ws->fork) {
+      CK(cudaEventCreateWithFlags(&ws->fork, cudaEventDisableTiming));
+      for (int l = 0; l < 4; ++l) {
+        CK(cudaStreamCreateWithFlags(&ws->side[l], cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ws->join[l], cudaEventDisableTiming));
+      }
+    }
+    const int ntiles = (m + MT - 1) / MT;
+    int64_t* it_all = buf<int64_t>(ws, "ln_it", m);
+    int* cv_all = buf<int>(ws, "ln_cv", m);
+    int64_t* inn_all = buf<int64_t>(ws, "ln_inn", lanes);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (o.profile) {
+      CK(cudaEventCreate(&t0));
+      CK(cudaEventCreate(&t1));
+      CK(cudaEventRecord(t0, st));
+    }
+    CK(cudaMemsetAsync(inn_all, 0, sizeof(int64_t) * lanes, st));
+    CK(cudaEventRecord(ws->fork, st));
+    for (int l = 0; l < lanes; ++l) CK(cudaStreamWaitEvent(ws->side[l], ws->fork, 0));
+    for (int t = 0; t < ntiles; ++t) {
+      const int l = t % lanes, c0 = t * MT, mc = std::min(MT, m - c0);
+      cudaStream_t sl = ws->side[l];
+      const std::string ls = "_l" + std::to_string(l);
+      SolverArgs a;
+      std::memset(&a, 0, sizeof(a));
+      a.mode = mode;
+      a.n = n;
+      a.A = sell_of(L.A);
+      if (mode == 1) a.M = sell_of(L.M);
+      if (mode == 2) {
+        a.seg_ptr = L.seg_ptr;
+        a.phi = L.phi_next;
+        a.nseg = L.nseg;
+      }
+      a.m = mc;
+      a.ld = n;
+      a.b = B ? (const char*)B + size_t(c0) * n * eb : nullptr;
+      a.x = X ? (char*)X + size_t(c0) * n * eb : nullptr;
+      a.b64 = B64 ? B64 + size_t(c0) * n : nullptr;
+      a.x64 = X64 ? X64 + size_t(c0) * n : nullptr;
+      a.x0 = x0;
+      a.r = buf<char>(ws, pre + "r" + ls, size_t(n) * MT * eb);
+      a.p = buf<char>(ws, pre + "p" + ls, size_t(n) * MT * eb);
+      a.q = buf<char>(ws, pre + "q" + ls, size_t(n) * MT * eb);
+      a.z = buf<char>(ws, pre + "z" + ls, size_t(n) * MT * eb);
+      a.ir = buf<char>(ws, pre + "ir" + ls, size_t(n) * MT * eb);
+      a.ip = buf<char>(ws, pre + "ip" + ls, size_t(n) * MT * eb);
+      a.iq = buf<char>(ws, pre + "iq" + ls, size_t(n) * MT * eb);
+      a.fp32 = fp32 ? 1 : 0;
+      a.tol = tol;
+      a.itol = 0.1 * tol;
+      a.maxit = maxit;
+      a.imaxit = std::min(maxit, 1000);
+      a.red = buf<double>(ws, "red" + ls, size_t(4) * 8 * 512);
+      a.it_out = it_all + c0;
+      a.in_out = inn_all + l;
+      a.conv = cv_all + c0;
+      unsigned* bar = buf<unsigned>(ws, "bar" + ls, 64);
+      a.bar.count = bar;
+      a.bar.gen = bar + 32;
+      a.bar.status = ws->status;
+      a.bar.timeout_ns = (long long)timeout_ns;
+      if (mode == 3) set_mg(a, mg_deg, mg_only, l);
+      CK(cudaMemsetAsync(bar, 0, sizeof(unsigned) * 64, sl));
+      CK(launch_solver(a, MT, grid, sl));
+      after_launch();
+    }
+    for (int l = 0; l < lanes; ++l) {
+      CK(cudaEventRecord(ws->join[l], ws->side[l]));
+      CK(cudaStreamWaitEvent(st, ws->join[l], 0));
+    }
+    if (o.profile) CK(cudaEventRecord(t1, st));
+    std::vector<int64_t> its(m), inn(lanes);
+    std::vector<int> cv(m);
+    CK(cudaMemcpyAsync(its.data(), it_all, sizeof(int64_t) * m, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(cv.data(), cv_all, sizeof(int) * m, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(inn.data(), inn_all, sizeof(int64_t) * lanes, cudaMemcpyDeviceToHost, st));
+    check_status();
+    double bytes = 0, flops = 0;
+    const double zA = (double)L.A.nnz, nn = (double)n;
+    const double mb = fp32 ? 8.0 : 12.0, vb = fp32 ? 4.0 : 8.0;
+    for (int t = 0; t < ntiles; ++t) {
+      const int c0 = t * MT, mc = std::min(MT, m - c0);
+      int64_t itmax = 0, itsum = 0;
+      for (int c = c0; c < c0 + mc; ++c) {
+        if (iters) iters->push_back(its[c]);
+        if (conv_out) conv_out->push_back(cv[c]);
+        if (!cv[c] && notconv) ++*notconv;
+        itmax = std::max(itmax, its[c]);
+        itsum += its[c];
+      }
+      bytes += itmax * (mb * zA + 4.0 * nn) + itsum * 9.0 * vb * nn;
+      flops += (double)itsum * (2.0 * zA + (mode == 2 ? 14.0 : 10.0) * nn);
+    }
+    int64_t inn_sum = 0;
+    for (auto v : inn) inn_sum += v;
+    if (mode == 1) {
+      bytes += (double)inn_sum * (mb * (double)L.M.nnz / MT + 7.5 * vb * nn);
+      flops += (double)inn_sum * (2.0 * (double)L.M.nnz + 10.0 * nn);
+    }
+    if (inner_total) *inner_total += inn_sum;
+    if (o.profile) {
+      // the concurrent tiles as one timed region (their launches overlap)
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, t0, t1));
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
+      S.pcg_launches += ntiles;
+      S.pcg_ms += ms;
+      S.pcg_bytes += bytes;
+      S.pcg_flops += flops;
+    }
+  }
 
   void solve_raw(int k, int mode, bool fp32, const void* B, void* X, int m, int x0, double tol, int maxit,
                  std::vector<int64_t>* iters, int64_t* inner_total, int* notconv, const double* B64 = nullptr,
@@ -398,6 +532,17 @@ struct Ctx {
     void* ir = buf<char>(ws, pre + "ir", size_t(n) * MT * eb);
     void* ip = buf<char>(ws, pre + "ip", size_t(n) * MT * eb);
     void* iq = buf<char>(ws, pre + "iq", size_t(n) * MT * eb);
+    const int ntiles = (m + MT - 1) / MT;
+    // several tiles: run them on up to four side streams at once, each grid on
+    // a quarter of the SMs (a tile's iteration is latency- and barrier-bound,
+    // so concurrent tiles overlap those waits); not inside the batched path,
+    // whose problems already share the SMs
+    const int lanes = (ntiles > 1 && coop_grid_cap() <= 0) ? std::min(ntiles, 4) : 1;
+    if (lanes > 1) {
+      solve_lanes(k, mode, fp32, B, X, m, x0, tol, maxit, iters, inner_total, notconv, B64, X64, conv_out, MT,
+                  std::max(1, std::min(grid, ws->nsm / lanes)), lanes);
+      return;
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     for (int c0 = 0; c0 < m; c0 += MT) {
       const int mc = std::min(MT, m - c0);
