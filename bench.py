@@ -218,7 +218,7 @@ def gpu_arm(args, rank, world):
 
     def step(profile, precision=prec, out=(lam, V)):
         return h.eig_leftmost(N, tol, out=out, allow_noconv=True, stream=sptr, profile=profile,
-                              precision=precision, mg_refine=args.mg_refine)[2]
+                              precision=precision, mg_refine=args.mg_refine, mg_op=args.mg_op)[2]
 
     def timed(steps, precision, out=(lam, V)):
         ev, sts = [], []
@@ -333,7 +333,8 @@ def gpu_arm(args, rank, world):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-        "config": dict(WORKLOAD, precision=args.precision, mg_refine=args.mg_refine, parallelism=f"replicas{world}"),
+        "config": dict(WORKLOAD, precision=args.precision, mg_refine=args.mg_refine, mg_op=args.mg_op,
+                       parallelism=f"replicas{world}"),
         "build_s": build_s,
         "residual": {"max_rel": st0["max_rel_residual"], "n_converged": st0["n_converged"]},
         "reference_eigs": reference_check(A, lam_main),
@@ -507,6 +508,8 @@ def main():
     ap.add_argument("--no-irlm", action="store_true", help="skip the IRLM-CG baseline step")
     ap.add_argument("--mg-refine", type=int, default=2,
                     help="Chebyshev degree of the V-cycle preconditioning the level-0 refinement (0: plain CG)")
+    ap.add_argument("--mg-op", type=int, default=0,
+                    help="Chebyshev degree of the V-cycle preconditioning the level-0 Lanczos OP solves (0: plain CG)")
     ap.add_argument("--budget-s", type=float, default=1500.0,
                     help="wall-clock budget of the run; optional legs are skipped past it")
     ap.add_argument("--kernel-case", choices=["op", "block", "eig", "spmv", "vcycle"], default=None)

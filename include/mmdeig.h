@@ -52,14 +52,18 @@ extern "C" {
 /* methods of eig_leftmost */
 #define MMD_HIERARCHICAL 0 /* Algorithm 6 on the decomposition (the paper's method) */
 #define MMD_IRLM_CG 1      /* Section 8's baseline: implicitly restarted Lanczos on A^{-1}, each
-                              application by plain CG, no decomposition (the extension of
+                              application by plain CG (or the polynomial PCG of poly_op when
+                              that is set), no decomposition (the extension of
                               Algorithm 4 at level 0 from an empty basis with searching step
                               d = N, i.e. N wanted and N shifts per restart) */
 
 /* precision modes of eig_leftmost */
 #define MMD_FP64 0      /* every step in FP64 */
 #define MMD_MIXED 1     /* coarse levels k >= 1: FP32 PCG inside FP64 iterative
-                           refinement; level 0 and all dense work in FP64 */
+                           refinement; level-0 CG on A in double-float arithmetic
+                           (FP32 pairs, ~48 bits) with its FP64 residual checked
+                           before a column is accepted (FP64 CG finishes a column
+                           it cannot); all dense work in FP64 */
 #define MMD_MIXED_ALL 2 /* as MMD_MIXED, and level-0 CG with FP32 recurrences and
                            FP64 reliable updates (for kappa(A) well below 1/u_32) */
 
@@ -116,7 +120,20 @@ typedef struct {
                           decomposition as a preconditioner (Section 2.3's A^{-1} representation
                           applied as an FP32 V-cycle over the levels, Chebyshev smoothing of this
                           degree; the outer PCG stays FP64 with the same stopping test).  0 = plain
-                          CG.  Default 2.  Lanczos OP solves keep plain CG (Section 4). */
+                          CG.  Default 2. */
+  int mg_op;           /* the same preconditioner, with this Chebyshev degree, for the level-0 solves
+                          of Operator OP inside the Lanczos extension (Algorithm 4 at level 0, where
+                          M^(0) = I leaves plain CG on A); OP's result, A^{-1}x to the same relative
+                          residual, is unchanged.  0 = plain CG.  MMD_IRLM_CG always uses plain CG. */
+  int poly_op;         /* level-0 Operator OP solves (Lanczos extension, and MMD_IRLM_CG's solves) by
+                          FP64 flexible PCG preconditioned by p(D^{-1}A) D^{-1}: this many steps of the
+                          Chebyshev iteration for A z = r on the interval [hi / poly_ratio, hi] of
+                          D^{-1}A (hi its Gershgorin bound), in FP32.  Same result (A^{-1}x to the same
+                          relative residual); trades grid-wide reductions and FP64 SpMVs for FP32 SpMVs.
+                          0 = off (plain CG, the default); takes precedence over mg_op.  <= 32. */
+  int poly_refine;     /* the same for the level-0 refinement solves; takes precedence over
+                          mg_refine.  0 = off (default). */
+  double poly_ratio;   /* hi / lo of the polynomial's interval (default 1000) */
 } mmd_eig_opts;
 
 /* Counters and timings of one eig_leftmost call (Section 7 reports the same
@@ -270,6 +287,15 @@ int mmd_level_bsolve(mmd_handle* h, int k, const double* q, double* x, double to
  *   inverse), FP32 arithmetic, FP64 in and out.  Needs K >= 1 and a coarsest
  *   level of at most 2048 rows (else MMD_EINVAL). */
 int mmd_level_vcycle(mmd_handle* h, int m, const double* R, double* Z, int deg, void* stream);
+/* mmd_level_poly: Z = p(D^{-1} A) D^{-1} R for m columns of level 0 (n x m,
+ *   column-major, device memory, natural order): one application of the
+ *   polynomial preconditioner of poly_op / poly_refine, i.e. deg (1..32)
+ *   steps of the Chebyshev iteration for A Z = R from Z = 0 on the interval
+ *   [hi / ratio, hi] of D^{-1} A (D = diag A, hi its Gershgorin bound;
+ *   ratio in (1, 1e12]); FP32 arithmetic, FP64 in and out.  The paper has
+ *   no counterpart: level 0 is plain CG in Section 4 (M^(0) = I), and this
+ *   operator only changes how A^{-1} x is reached, not its value. */
+int mmd_level_poly(mmd_handle* h, int m, const double* R, double* Z, int deg, double ratio, void* stream);
 
 /* The SpMV autotuner: when a level matrix is uploaded the library times each
  * single-column SELL SpMV kernel variant on it (entries in flight per lane

@@ -39,9 +39,10 @@ def gershgorin(A: sp.spmatrix) -> float:
     return float((np.asarray(abs(A).sum(axis=1)).ravel() / A.diagonal()).max())
 
 
-def chebyshev(A, dinv, b, x0, deg: int, hi: float):
+def chebyshev(A, dinv, b, x0, deg: int, hi: float, lo: float | None = None):
     """deg steps of Chebyshev iteration for A x = b preconditioned by D^{-1},
-    eigenvalue interval [hi * LO_FRACTION, hi] (x0 None means x0 = 0).
+    eigenvalue interval [lo, hi], lo = hi * LO_FRACTION unless given (x0 None
+    means x0 = 0).
 
     theta = (hi + lo) / 2, delta = (hi - lo) / 2, sigma = theta / delta;
     d_0 = D^{-1}(b - A x_0) / theta;  rho_0 = 1 / sigma;
@@ -49,7 +50,8 @@ def chebyshev(A, dinv, b, x0, deg: int, hi: float):
     d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / delta) D^{-1}(b - A x_k);
     x_{k+1} = x_k + d_k.  The error obeys e_deg = T_deg((theta - D^{-1}A)/delta)
     / T_deg(sigma) e_0 (T the Chebyshev polynomial of the first kind)."""
-    lo = hi * LO_FRACTION
+    if lo is None:
+        lo = hi * LO_FRACTION
     theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
     sigma = theta / delta
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
@@ -97,7 +99,33 @@ class VCycle:
         return np.stack([self.cycle(r[:, c]) for c in range(r.shape[1])], axis=1)
 
 
-def mg_pcg(A, b, P: VCycle, x0=None, tol=1e-8, maxit=100000):
+class PolyPrec:
+    """The polynomial preconditioner of the level-0 solves:
+    z = p(D^{-1}A) D^{-1} r, ``deg`` steps of ``chebyshev`` for A z = r from
+    z = 0 on the interval [hi / ratio, hi] of D^{-1} A.  Not in the paper
+    (its level 0 is not computed, and Operator OP there is PCG with M^(k),
+    which is the identity at level 0); it changes how A^{-1} b is reached,
+    not its value.  With the residual polynomial R(t) = T_deg((theta - t) /
+    delta) / T_deg(theta / delta) of the interval, the operator is
+    (I - R(D^{-1}A)) A^{-1}: symmetric, and positive definite when
+    |R| < 1 on the spectrum of D^{-1} A, which holds on (0, hi]."""
+
+    def __init__(self, A, deg: int = 16, ratio: float = 1000.0):
+        self.A = sp.csr_matrix(A)
+        self.deg = deg
+        self.dinv = 1.0 / self.A.diagonal()
+        self.hi = gershgorin(self.A)
+        self.lo = self.hi / ratio
+
+    def __call__(self, r):
+        r = np.asarray(r, dtype=np.float64)
+        if r.ndim == 1:
+            return chebyshev(self.A, self.dinv, r, None, self.deg, self.hi, self.lo)
+        return np.stack([chebyshev(self.A, self.dinv, r[:, c], None, self.deg, self.hi, self.lo)
+                         for c in range(r.shape[1])], axis=1)
+
+
+def mg_pcg(A, b, P, x0=None, tol=1e-8, maxit=100000):
     """Flexible PCG (the update of solvers.fpcg) with z = P(r).
     Returns (x, iterations, converged)."""
     b = np.asarray(b, dtype=np.float64)

@@ -145,6 +145,12 @@ class MMD:
         _lib.check(self._lib.mmd_level_vcycle(self.h, R.shape[0], R.data_ptr(), Z.data_ptr(), deg, stream),
                    "mmd_level_vcycle")
 
+    def level_poly(self, R, Z, deg=16, ratio=1000.0, stream=0):
+        """Z = p(D^{-1}A) D^{-1} R: one application of the level-0 polynomial
+        preconditioner; R, Z: CUDA float64 tensors (m, n), one row per column."""
+        _lib.check(self._lib.mmd_level_poly(self.h, R.shape[0], R.data_ptr(), Z.data_ptr(), deg, ratio, stream),
+                   "mmd_level_poly")
+
     def level_bsolve(self, k, q, x, tol, max_iter=20000, stream=0) -> int:
         it = C.c_int64(0)
         _lib.check(self._lib.mmd_level_bsolve(self.h, k, q.data_ptr(), x.data_ptr(), tol, max_iter, C.byref(it),

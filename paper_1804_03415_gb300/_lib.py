@@ -36,7 +36,8 @@ class mmd_eig_opts(C.Structure):
                 ("precision", C.c_int), ("max_cg_iter", C.c_int), ("max_restarts", C.c_int),
                 ("max_refine_iter", C.c_int), ("timeout_s", C.c_double), ("seed", C.c_uint64),
                 ("stream", C.c_void_p), ("profile", C.c_int), ("method", C.c_int), ("stop_level", C.c_int),
-                ("mg_refine", C.c_int)]
+                ("mg_refine", C.c_int), ("mg_op", C.c_int),
+                ("poly_op", C.c_int), ("poly_refine", C.c_int), ("poly_ratio", C.c_double)]
 
 
 class mmd_eig_stats(C.Structure):
@@ -88,6 +89,7 @@ SIGNATURES = {
                                      C.c_void_p, C.c_int, C.c_void_p]),
     "mmd_spmv_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "mmd_level_vcycle": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "mmd_level_poly": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p]),
     "mmd_level_bsolve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                    C.POINTER(C.c_int64), C.c_void_p]),
     "mmd_free": (None, [C.c_void_p]),

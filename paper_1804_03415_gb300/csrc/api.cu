@@ -190,6 +190,13 @@ static int upload_csr(const HCSR& A, DCSR& D) {
   if ((rc = dput(&D.s_val, sval))) return rc;
   std::vector<float> sv32(sval.begin(), sval.end());
   if ((rc = dput(&D.s_val32, sv32))) return rc;
+  std::vector<float> sv2(2 * tot);
+  for (int64_t i = 0; i < tot; ++i) {
+    const float hi = (float)sval[i];
+    sv2[2 * i] = hi;
+    sv2[2 * i + 1] = (float)(sval[i] - (double)hi);
+  }
+  if ((rc = dput(&D.s_val2, sv2))) return rc;
   return autotune_spmv(D);
 }
 
@@ -277,6 +284,7 @@ static void free_csr(DCSR& D) {
   cudaFree(D.s_col);
   cudaFree(D.s_val);
   cudaFree(D.s_val32);
+  cudaFree(D.s_val2);
   D = DCSR();
 }
 
@@ -319,6 +327,25 @@ int upload_levels(mmd_handle* h) {
     if ((rc = dput(&L.d_perm, perm[k]))) return rc;
     if ((rc = dput(&L.d_iperm, iperm[k]))) return rc;
   }
+  // 1 / diag (FP32, device order) and the Gershgorin bound of D^{-1} A^(k):
+  // level 0 always (the polynomial preconditioner of the level-0 solves),
+  // the other smoothed levels with the V-cycle
+  auto diag_data = [&](int k) -> int {
+    DLevel& L = h->dl[k];
+    if (L.dinv32) return MMD_OK;
+    const HCSR& A = (k == 0) ? h->A0 : h->levels[k - 1].A;
+    L.gersh = gershgorin(A);
+    std::vector<float> dinv(A.nrows);
+    for (int64_t i = 0; i < A.nrows; ++i) {
+      const int32_t r = perm[k][i];
+      double d = 0;
+      for (int32_t e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e)
+        if (A.col[e] == r) d = A.val[e];
+      dinv[i] = (float)(1.0 / d);
+    }
+    return dput(&L.dinv32, dinv);
+  };
+  if ((rc = diag_data(0))) return rc;
   // V-cycle preconditioner of the level-0 refinement solves: Psi^T per level,
   // 1 / diag and the Gershgorin bound per smoothed level, the coarsest inverse
   h->mg_ok = false;
@@ -328,18 +355,7 @@ int upload_levels(mmd_handle* h) {
     const HCSR& AK = h->levels[K - 1].A;
     if (spd_inverse(AK, inv)) {
       for (int k = 0; k < K; ++k) {
-        DLevel& L = h->dl[k];
-        const HCSR& A = (k == 0) ? h->A0 : h->levels[k - 1].A;
-        L.gersh = gershgorin(A);
-        std::vector<float> dinv(A.nrows);
-        for (int64_t i = 0; i < A.nrows; ++i) {  // device order
-          const int32_t r = perm[k][i];
-          double d = 0;
-          for (int32_t e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e)
-            if (A.col[e] == r) d = A.val[e];
-          dinv[i] = (float)(1.0 / d);
-        }
-        if ((rc = dput(&L.dinv32, dinv))) return rc;
+        if ((rc = diag_data(k))) return rc;
         const HLevel& H = h->levels[k];
         if ((rc = upload_csr(transpose(permute_rect(H.psi, perm[k], iperm[k + 1])), h->dl[k + 1].psiT))) return rc;
       }
@@ -407,6 +423,10 @@ void mmd_default_eig_opts(mmd_eig_opts* o) {
   o->method = MMD_HIERARCHICAL;
   o->stop_level = 0;
   o->mg_refine = 2;
+  o->mg_op = 0;
+  o->poly_op = 0;
+  o->poly_refine = 0;
+  o->poly_ratio = 1000.0;
 }
 
 int mmd_build(const mmd_csr* A, const mmd_build_opts* opts, mmd_handle** out) {
@@ -594,6 +614,15 @@ int mmd_level_vcycle(mmd_handle* h, int m, const double* R, double* Z, int deg, 
   return level_vcycle(h, m, R, Z, deg, (cudaStream_t)stream);
 }
 
+int mmd_level_poly(mmd_handle* h, int m, const double* R, double* Z, int deg, double ratio, void* stream) {
+  if (!h || !h->on_device || m < 1 || !R || !Z || deg < 1 || deg > 32 || !(ratio > 1.0) || !std::isfinite(ratio) ||
+      ratio > 1e12) {
+    set_error("mmd_level_poly: bad arguments");
+    return MMD_EINVAL;
+  }
+  return level_poly(h, m, R, Z, deg, ratio, (cudaStream_t)stream);
+}
+
 int mmd_level_bsolve(mmd_handle* h, int k, const double* q, double* x, double tol, int max_iter, int64_t* iters,
                      void* stream) {
   if (!h || !h->on_device || k < 1 || k > (int)h->levels.size() || !q || !x || !(tol > 0) || max_iter < 1) {
@@ -624,6 +653,11 @@ static bool validated_opts(const mmd_eig_opts* opts, const char* who, mmd_eig_op
   else if (o.stop_level < 0 || o.stop_level > 16) bad = "stop_level must be in [0, K]";
   else if (o.method == MMD_IRLM_CG && o.stop_level != 0) bad = "stop_level applies to MMD_HIERARCHICAL only";
   else if (o.mg_refine < 0 || o.mg_refine > 8) bad = "mg_refine must be in [0, 8]";
+  else if (o.mg_op < 0 || o.mg_op > 8) bad = "mg_op must be in [0, 8]";
+  else if (o.poly_op < 0 || o.poly_op > 32 || o.poly_refine < 0 || o.poly_refine > 32)
+    bad = "poly_op and poly_refine must be in [0, 32]";
+  else if (!(o.poly_ratio > 1.0) || !std::isfinite(o.poly_ratio) || o.poly_ratio > 1e12)
+    bad = "poly_ratio must be finite, > 1 and <= 1e12";
   if (!bad.empty()) {
     set_error(std::string(who) + ": invalid options: " + bad);
     return false;

@@ -143,6 +143,7 @@ Sell sell_of(const DCSR& A) {
   s.col = A.s_col;
   s.val = A.s_val;
   s.val32 = A.s_val32;
+  s.val2 = reinterpret_cast<const float2*>(A.s_val2);
   s.variant = A.spmv_variant;
   return s;
 }
@@ -244,11 +245,40 @@ struct Ctx {
   // level 0 too).
   void solve(int k, int mode, const double* B, double* X, int m, int x0, double tol, int maxit,
              std::vector<int64_t>* iters, int64_t* inner_total, int* notconv) {
+    if (o.precision == MMD_MIXED && k == 0 && mode == 0 && h->dl[0].A.s_val2) {
+      solve_df(B, X, m, x0, tol, maxit, iters, inner_total, notconv);
+      return;
+    }
     if ((o.precision == MMD_MIXED && k >= 1) || o.precision == MMD_MIXED_ALL) {
       solve_mixed(k, mode, B, X, m, x0, tol, maxit, iters, inner_total, notconv);
       return;
     }
     solve_raw(k, mode, false, B, X, m, x0, tol, maxit, iters, inner_total, notconv);
+  }
+
+  // Level-0 CG on A in double-float arithmetic (FP32 pairs, the matrix's
+  // pair copy), checked against the FP64 residual b - A x before a column
+  // is accepted; columns it leaves unconverged continue in FP64 CG from
+  // their current x.
+  bool use_df = false;
+  void solve_df(const double* B, double* X, int m, int x0, double tol, int maxit, std::vector<int64_t>* iters,
+                int64_t* inner_total, int* notconv) {
+    std::vector<int64_t> its;
+    std::vector<int> cv;
+    use_df = true;
+    solve_raw(0, 0, false, B, X, m, x0, tol, maxit, &its, inner_total, nullptr, nullptr, nullptr, &cv);
+    use_df = false;
+    const int64_t n = h->dl[0].n;
+    for (int c = 0; c < m; ++c) {
+      if (!cv[c]) {
+        std::vector<int64_t> its64;
+        solve_raw(0, 0, false, B + size_t(c) * n, X + size_t(c) * n, 1, 1, tol, maxit, &its64, inner_total,
+                  notconv);
+        its[c] += its64[0];
+        S.fp64_finishes += 1;
+      }
+      if (iters) iters->push_back(its[c]);
+    }
   }
 
   // FP64 iterative refinement: R = B - A X in FP64, FP32 solve A D = R to a
@@ -380,6 +410,35 @@ struct Ctx {
   }
   int mg_deg = 2, mg_only = 0;
 
+  // The polynomial preconditioner of level 0 (mode 4): Chebyshev coefficients
+  // of degree deg on [hi / poly_ratio, hi] (hi: Gershgorin bound of D^{-1} A)
+  // and FP32 work vectors for tiles of up to four columns.
+  void set_poly(SolverArgs& a, int deg, int lane = 0) {
+    const DLevel& L = h->dl[0];
+    PolyPrec& P = a.poly;
+    P.deg = deg;
+    const double hi = L.gersh, lo = hi / o.poly_ratio, th = 0.5 * (hi + lo), de = 0.5 * (hi - lo), sg = th / de;
+    double rho = 1.0 / sg;
+    P.c1[0] = 0.f;
+    P.c2[0] = (float)(1.0 / th);
+    for (int st = 1; st < 32; ++st) {
+      const double rn = 1.0 / (2.0 * sg - rho);
+      P.c1[st] = (float)(rn * rho);
+      P.c2[st] = (float)(2.0 * rn / de);
+      rho = rn;
+    }
+    P.dinv = L.dinv32;
+    P.cA = csr32_of(L.A, ws->nsm);
+    const int MTmax = 4;
+    const std::string t = "_" + std::to_string(lane);
+    P.r = buf<float>(ws, "pl_r" + t, size_t(L.n) * MTmax);
+    P.x = buf<float>(ws, "pl_x" + t, size_t(L.n) * MTmax);
+    P.x2 = buf<float>(ws, "pl_y" + t, size_t(L.n) * MTmax);
+    P.d = buf<float>(ws, "pl_d" + t, size_t(L.n) * MTmax);
+    a.mg_only = mg_only;
+  }
+  int poly_deg = 0;
+
   // Tiles of MT columns distributed round-robin over `lanes` side streams,
   // each lane with its own vectors, reduction partials, barrier counter and
   // result slots; the caller's stream forks to and joins the lanes by events.
@@ -440,6 +499,7 @@ struct Ctx {
       a.ip = buf<char>(ws, pre + "ip" + ls, size_t(n) * MT * eb);
       a.iq = buf<char>(ws, pre + "iq" + ls, size_t(n) * MT * eb);
       a.fp32 = fp32 ? 1 : 0;
+      a.df = (use_df && mode == 0 && !fp32) ? 1 : 0;
       a.tol = tol;
       a.itol = 0.1 * tol;
       a.maxit = maxit;
@@ -454,6 +514,7 @@ struct Ctx {
       a.bar.status = ws->status;
       a.bar.timeout_ns = (long long)timeout_ns;
       if (mode == 3) set_mg(a, mg_deg, mg_only, l);
+      if (mode == 4) set_poly(a, poly_deg, l);
       CK(cudaMemsetAsync(bar, 0, sizeof(unsigned) * 64, sl));
       CK(launch_solver(a, MT, grid, sl));
       after_launch();
@@ -572,6 +633,7 @@ struct Ctx {
       a.ip = ip;
       a.iq = iq;
       a.fp32 = fp32 ? 1 : 0;
+      a.df = (use_df && mode == 0 && !fp32) ? 1 : 0;
       a.tol = tol;
       a.itol = 0.1 * tol;
       a.maxit = maxit;
@@ -585,6 +647,7 @@ struct Ctx {
       a.bar.status = ws->status;
       a.bar.timeout_ns = (long long)timeout_ns;
       if (mode == 3) set_mg(a, mg_deg, mg_only);
+      if (mode == 4) set_poly(a, poly_deg);
       CK(cudaMemsetAsync(ws->in_out, 0, sizeof(int64_t), st));
       CK(cudaMemsetAsync(ws->bar, 0, sizeof(unsigned), st));
       if (o.profile) {
@@ -644,7 +707,19 @@ struct Ctx {
     std::vector<int64_t> its;
     int64_t inner = 0;
     int nc = 0;
-    solve(k, k == 0 ? 0 : 1, b, y, 1, 0, tol, o.max_cg_iter, &its, &inner, &nc);
+    if (k == 0 && o.poly_op > 0 && h->dl[0].dinv32) {
+      // A^{-1} x by FP64 PCG preconditioned by a Chebyshev polynomial in D^{-1} A
+      poly_deg = o.poly_op;
+      mg_only = 0;
+      solve_raw(0, 4, false, b, y, 1, 0, tol, o.max_cg_iter, &its, &inner, &nc);
+    } else if (k == 0 && h->mg_ok && o.mg_op > 0 && o.method == MMD_HIERARCHICAL) {
+      // A^{-1} x by FP64 PCG preconditioned by the decomposition's V-cycle
+      mg_deg = o.mg_op;
+      mg_only = 0;
+      solve_raw(0, 3, false, b, y, 1, 0, tol, o.max_cg_iter, &its, &inner, &nc);
+    } else {
+      solve(k, k == 0 ? 0 : 1, b, y, 1, 0, tol, o.max_cg_iter, &its, &inner, &nc);
+    }
     S.op_calls += 1;
     S.pcg_iters += its[0];
     S.inner_iters += inner;
@@ -1011,7 +1086,12 @@ int refine(Ctx& c, int k, double* Q0, std::vector<double>& D, double tol_rel, do
       std::vector<int64_t> its;
       int64_t inner = 0;
       int nc = 0;
-      if (k == 0 && c.h->mg_ok && c.o.mg_refine > 0) {
+      if (k == 0 && c.o.poly_refine > 0 && c.h->dl[0].dinv32) {
+        // warm-started level-0 solves preconditioned by a Chebyshev polynomial (FP32, FP64 PCG)
+        c.poly_deg = c.o.poly_refine;
+        c.mg_only = 0;
+        c.solve_raw(0, 4, false, W, F, m, 1, tol_rel, c.o.max_cg_iter, &its, &inner, &nc);
+      } else if (k == 0 && c.h->mg_ok && c.o.mg_refine > 0) {
         // warm-started level-0 solves preconditioned by the decomposition (FP32 V-cycle, FP64 PCG)
         c.mg_deg = c.o.mg_refine;
         c.mg_only = 0;
@@ -1236,6 +1316,31 @@ int level_op_block(mmd_handle* h, int k, int m, const double* x, double* y, doub
       set_error("mmd_level_op_block: PCG reached max_iter");
       return MMD_ENOCONV;
     }
+  } catch (const CudaFail& f) {
+    return f.code;
+  }
+  return MMD_OK;
+}
+
+int level_poly(mmd_handle* h, int m, const double* R, double* Z, int deg, double ratio, cudaStream_t st) {
+  try {
+    mmd_eig_opts o;
+    mmd_default_eig_opts(&o);
+    o.poly_ratio = ratio;
+    Ctx c(h, st, o);
+    CK(cudaMemsetAsync(c.ws->status, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(c.ws->bar, 0, 2 * sizeof(unsigned), st));
+    const DLevel& L = h->dl[0];
+    double* a = buf<double>(c.ws, "lv_a", size_t(L.n) * m);
+    double* b = buf<double>(c.ws, "lv_b", size_t(L.n) * m);
+    k_gather(R, L.n, L.d_perm, L.n, m, a, L.n, st);
+    c.poly_deg = deg;
+    c.mg_only = 1;
+    std::vector<int64_t> its;
+    c.solve_raw(0, 4, false, a, b, m, 0, 1e-30, 1, &its, nullptr, nullptr);
+    k_scatter(b, L.n, L.d_perm, L.n, m, Z, L.n, st);
+    c.sync();
+    CK(cudaGetLastError());
   } catch (const CudaFail& f) {
     return f.code;
   }

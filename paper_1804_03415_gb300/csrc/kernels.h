@@ -18,6 +18,7 @@ struct Sell {
   const int32_t* col = nullptr;
   const double* val = nullptr;
   const float* val32 = nullptr;
+  const float2* val2 = nullptr;  // double-float copy: value = hi + lo
   int variant = -1;  // single-column SpMV kernel picked by k_spmv_autotune (-1: not tuned)
 };
 
@@ -47,8 +48,21 @@ struct MGLevel {
   float *r, *x, *x2, *d;  // n x MT each: right-hand side, iterate (ping-pong), direction / residual
 };
 
+// Polynomial preconditioner of the level-0 solves (mode 4, FP32 work):
+// z = p(D^{-1} A) D^{-1} r, deg steps of the Chebyshev iteration for A z = r
+// from z = 0 on the interval [hi / ratio, hi] of D^{-1} A (hi its Gershgorin
+// bound); step st: d = c1[st] d + c2[st] D^{-1} (r - A x), x += d (c1[0] = 0).
+struct PolyPrec {
+  int deg;
+  float c1[32], c2[32];
+  const float* dinv;      // n
+  Csr32 cA;               // CSR view of A (g > 0: rows shared by g lanes)
+  float *r, *x, *x2, *d;  // n x MT each, interleaved
+};
+
 struct SolverArgs {
-  int mode;  // 0 CG, 1 flexible PCG with inner CG on M, 2 CG on P A P, 3 flexible PCG with the V-cycle
+  int mode;  // 0 CG, 1 flexible PCG with inner CG on M, 2 CG on P A P, 3 flexible PCG with the V-cycle,
+             // 4 flexible PCG with the Chebyshev polynomial preconditioner
   int64_t n;
   Sell A;
   Sell M;
@@ -63,6 +77,7 @@ struct SolverArgs {
   void *r, *p, *q, *z;
   void *ir, *ip, *iq;
   int fp32;        // 1: FP32 instance (matrix val32, FP32 vectors)
+  int df;          // 1: double-float CG (mode 0): matrix val2, vectors as FP32 pairs, FP64 b and x
   // mode 0 with fp32 = 1 and b64 != NULL: FP32 CG with FP64 reliable updates;
   // b64 / x64 (n x m, ld) are the FP64 right-hand side and solution
   const double* b64;
@@ -81,6 +96,7 @@ struct SolverArgs {
   float *mg_rK, *mg_xK;  // nK x MT
   int64_t mg_nK;
   int mg_only;  // 1: apply z = V(b) once (x = z, column-major) instead of solving
+  PolyPrec poly;  // mode 4
 };
 
 int solver_threads(int mt);

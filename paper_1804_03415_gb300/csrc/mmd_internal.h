@@ -45,6 +45,7 @@ struct DCSR {
   int32_t* s_col = nullptr;   // sell_nnz
   double* s_val = nullptr;    // sell_nnz
   float* s_val32 = nullptr;   // sell_nnz
+  float* s_val2 = nullptr;    // 2 x sell_nnz: each value as the pair (hi, lo) of FP32 numbers, value = hi + lo
   int spmv_variant = -1;      // single-column SpMV kernel chosen by the autotuner at upload
   std::vector<float> spmv_ms; // its timing of every variant (ms)
 };

@@ -562,6 +562,62 @@ __device__ __forceinline__ bool mg_vcycle(const SolverArgs& a, const int* act) {
   return true;
 }
 
+// z = p(D^{-1} A) D^{-1} r for the columns with act[c] (mode 4): deg steps
+// of the Chebyshev iteration for A z = r from z = 0, FP32, one pass over the
+// rows and one grid barrier per step and no reduction, so a preconditioned
+// iteration trades deg - 1 cheap FP32 SpMVs for the grid-wide reduction
+// rounds (and FP64 SpMVs) of the CG iterations it saves.  The other columns'
+// z is left alone.
+template <int MT>
+__device__ __forceinline__ bool cheb_prec(const SolverArgs& a, const int* act) {
+  const PolyPrec& P = a.poly;
+  const double* __restrict__ r0 = (const double*)a.r;
+  double* __restrict__ z0 = (double*)a.z;
+  const int deg = P.deg;
+  int on[MT];
+#pragma unroll
+  for (int c = 0; c < MT; ++c) on[c] = (c < a.m) && act[c];
+  float* x = P.x;
+  float* x2 = P.x2;
+  float* __restrict__ rr = P.r;
+  float* __restrict__ dd = P.d;
+  const float* __restrict__ dinv = P.dinv;
+  const float c0 = P.c2[0];
+  FOR_BLOCK_SHARE(i, a.n)
+    _Pragma("unroll") for (int c = 0; c < MT; ++c) {
+      const int64_t o = wix<MT>(i, c);
+      const float rv = on[c] ? (float)r0[o] : 0.f;
+      rr[o] = rv;
+      const float dv = c0 * dinv[i] * rv;
+      dd[o] = dv;
+      x[o] = dv;
+      if (deg == 1 && on[c]) z0[o] = (double)dv;
+    }
+  if (!grid_sync(a.bar)) return false;
+  for (int st = 1; st < deg; ++st) {
+    const float c1 = P.c1[st], c2 = P.c2[st];
+    const bool out = (st == deg - 1);
+    const float* xs = x;
+    float* xd = x2;
+    mg_apply<MT>(a.A, P.cA, xs, [&](int32_t row, const float* acc) {
+#pragma unroll
+      for (int c = 0; c < MT; ++c) {
+        const int64_t o = wix<MT>(row, c);
+        const float dv = fmaf(c1, dd[o], c2 * dinv[row] * (rr[o] - acc[c]));
+        dd[o] = dv;
+        const float xn = xs[o] + dv;
+        xd[o] = xn;
+        if (out && on[c]) z0[o] = (double)xn;
+      }
+    });
+    if (!grid_sync(a.bar)) return false;
+    float* t = x;
+    x = x2;
+    x2 = t;
+  }
+  return true;
+}
+
 // Mode 0: CG in the Chronopoulos-Gear form: r^T r and r^T A r are both
 // formed in the SpMV pass (w = A r), so an iteration has one reduction round
 // (block sums, grid barrier, partials) and one plain grid barrier before the
@@ -824,8 +880,385 @@ __device__ bool cg_rel(const SolverArgs& a, Sh<MT>& s) {
   return true;
 }
 
-// VC = 1: the instance with the V-cycle preconditioner (mode 3), kept apart
-// so that the other modes' register allocation does not see the call.
+// ---- double-float arithmetic (the level-0 CG of MMD_MIXED)
+//
+// A value is the unevaluated sum hi + lo of two FP32 numbers, |lo| <= half
+// an ulp of hi: about 48 significant bits, the exponent range of FP32.  The
+// error-free transformations are Knuth's two-sum (s + e = a + b exactly) and
+// the FMA two-product (p + e = a b exactly); the pair operations follow
+// Dekker (1971) and the GPU formulation of Thall (2006), "sloppy" addition
+// (the low parts added without their own two-sum: error below 2^-44 of the
+// operands' magnitude).  Every step uses the rounded intrinsics, so the
+// compiler neither contracts a step into an FMA nor reassociates.  GB300
+// issues FP32 about seventy times faster than FP64 (one FP64 FMA per 64
+// cycles per warp on an SM sub-partition), so the 15 FP32 operations of a
+// pair FMA cost about a quarter of one FP64 FMA.
+struct dd {
+  float hi, lo;
+};
+__device__ __forceinline__ dd dd_of(double v) {
+  const float h = __double2float_rn(v);
+  return {h, __double2float_rn(v - (double)h)};
+}
+__device__ __forceinline__ double dd_val(dd a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dd dd_renorm(float s, float e) {  // |s| >= |e| or s = 0
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return dd_renorm(s, e);
+}
+// a b + c
+__device__ __forceinline__ dd dd_fma(dd a, dd b, dd c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float pe = __fmaf_rn(a.hi, b.hi, -p);
+  pe = __fmaf_rn(a.hi, b.lo, pe);
+  pe = __fmaf_rn(a.lo, b.hi, pe);
+  const float s = __fadd_rn(p, c.hi);
+  const float bb = __fsub_rn(s, p);
+  float e = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(c.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(pe, c.lo));
+  return dd_renorm(s, e);
+}
+__device__ __forceinline__ dd dd_neg(dd a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dd dd_warp_sum(dd v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dd t;
+    t.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    t.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = dd_add(v, t);
+  }
+  return v;
+}
+
+// The MT values X(j, 0..MT-1) of an interleaved pair vector.
+template <int MT>
+__device__ __forceinline__ void load_row_dd(const dd* __restrict__ X, int64_t j, dd* v) {
+  if constexpr (MT == 1) {
+    const float2 t = reinterpret_cast<const float2*>(X)[j];
+    v[0] = {t.x, t.y};
+  } else {
+    const float4* q = reinterpret_cast<const float4*>(X + j * MT);
+#pragma unroll
+    for (int h = 0; h < MT / 2; ++h) {
+      const float4 t = q[h];
+      v[2 * h] = {t.x, t.y};
+      v[2 * h + 1] = {t.z, t.w};
+    }
+  }
+}
+
+// Y(:,c) = A X(:,c) in pair arithmetic (SELL-32, one row per lane, values
+// val2), and dacc[c] += W(row,c) Y(row,c), dacc2[c] += W(row,c)^2.
+template <int MT>
+__device__ __forceinline__ void spmv_dd(const Sell& A, const dd* __restrict__ X, dd* __restrict__ Y, int m,
+                                        const int* mask, const dd* __restrict__ W, dd* dacc, dd* dacc2) {
+  const float2* __restrict__ vals = A.val2;
+  const int lane = threadIdx.x & 31;
+  int msk[MT];
+#pragma unroll
+  for (int c = 0; c < MT; ++c) msk[c] = (c < m) && mask[c];
+  FOR_BLOCK_SLICES(sl, A.nslices) {
+    const int32_t base = A.ptr[sl] + lane, len = A.len[sl];
+    const int32_t row = A.row[sl * 32 + lane];
+    dd acc[MT];
+#pragma unroll
+    for (int c = 0; c < MT; ++c) acc[c] = {0.f, 0.f};
+    int32_t k = 0;
+    constexpr int U = (MT == 1) ? 4 : 2;  // entries in flight
+    for (; k + U <= len; k += U) {
+      float2 a[U];
+      int64_t j[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        a[u] = vals[base + (k + u) * 32];
+        j[u] = A.col[base + (k + u) * 32];
+      }
+      dd xv[U][MT];
+#pragma unroll
+      for (int u = 0; u < U; ++u) load_row_dd<MT>(X, j[u], xv[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int c = 0; c < MT; ++c)
+          if (msk[c]) acc[c] = dd_fma({a[u].x, a[u].y}, xv[u][c], acc[c]);
+    }
+    for (; k < len; ++k) {
+      const float2 av = vals[base + k * 32];
+      dd xv[MT];
+      load_row_dd<MT>(X, A.col[base + k * 32], xv);
+#pragma unroll
+      for (int c = 0; c < MT; ++c)
+        if (msk[c]) acc[c] = dd_fma({av.x, av.y}, xv[c], acc[c]);
+    }
+    if (row >= 0) {
+#pragma unroll
+      for (int c = 0; c < MT; ++c)
+        if (msk[c]) {
+          Y[wix<MT>(row, c)] = acc[c];
+          const dd wv = W[wix<MT>(row, c)];
+          dacc[c] = dd_fma(wv, acc[c], dacc[c]);
+          dacc2[c] = dd_fma(wv, wv, dacc2[c]);
+        }
+    }
+  }
+}
+
+// Block sums of acc[c] (slot) and acc2[c] (slot2), c < m, in pair
+// arithmetic: warp shuffles, one pair per warp in shared memory, then warp v
+// adds the block's warp pairs of value v and stores red[slot][c][blockIdx]
+// as a float2; no FP64 instruction.  Fixed order: deterministic.
+template <int MT>
+__device__ __forceinline__ void write_partials_dd(float2* red, int slot, int m, const dd* acc, int slot2,
+                                                  const dd* acc2) {
+  float2* sh = reinterpret_cast<float2*>(g_part);  // [2 MT][32]
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int c = 0; c < MT; ++c)
+    if (c < m) {
+      const dd a = dd_warp_sum(acc[c]);
+      const dd b = dd_warp_sum(acc2[c]);
+      if (lane == 0) {
+        sh[c * 32 + w] = make_float2(a.hi, a.lo);
+        sh[(MT + c) * 32 + w] = make_float2(b.hi, b.lo);
+      }
+    }
+  __syncthreads();
+  if (w < 2 * m) {
+    const int v = w < m ? w : MT + (w - m);
+    const int c = w < m ? w : w - m;
+    dd t = {0.f, 0.f};
+    if (lane < nw) {
+      const float2 q = sh[v * 32 + lane];
+      t = {q.x, q.y};
+    }
+    t = dd_warp_sum(t);
+    if (lane == 0) red[(size_t(w < m ? slot : slot2) * MT + c) * gridDim.x + blockIdx.x] = make_float2(t.hi, t.lo);
+  }
+}
+
+// red[slot][c][*] -> dst[c] and red[slot2][c][*] -> dst2[c] (FP64, shared),
+// the partials added in pair arithmetic.
+template <int MT>
+__device__ __forceinline__ void reduce_slot_dd(const float2* red, int slot, int m, double* dst, int slot2,
+                                               double* dst2) {
+  const int G = gridDim.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < 2 * m) {
+    const int c = w < m ? w : w - m;
+    const float2* p = red + (size_t(w < m ? slot : slot2) * MT + c) * G;
+    dd t = {0.f, 0.f};
+    for (int b = lane; b < G; b += 32) t = dd_add(t, {p[b].x, p[b].y});
+    t = dd_warp_sum(t);
+    if (lane == 0) (w < m ? dst : dst2)[c] = dd_val(t);
+  }
+  __syncthreads();
+}
+
+// r = b - A x in FP64 (x: the caller's FP64 column-major solution; q64:
+// interleaved FP64 scratch), stored as pairs in r and rr[c] = ||r_c||^2;
+// columns without mask[c] are skipped.  With first, x = 0 is taken and no
+// product is formed.
+template <int MT>
+__device__ bool dd_true_residual(const SolverArgs& a, Sh<MT>& s, const int* mask, bool first, double* rr) {
+  const double* __restrict__ b = (const double*)a.b;
+  const double* __restrict__ x = (const double*)a.x;
+  double* q64 = (double*)a.ip;
+  dd* r = (dd*)a.r;
+  const int m = a.m;
+  const int64_t n = a.n, ld = a.ld;
+  double dummy[MT];
+  if (!first) {
+    spmv_cols<MT, double, false>(a.A, x, ld, q64, m, mask, nullptr, dummy);
+    if (!grid_sync(a.bar)) return false;
+  }
+  double acc[MT];
+#pragma unroll
+  for (int c = 0; c < MT; ++c) acc[c] = 0.0;
+  FOR_BLOCK_SHARE(i, n)
+    _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m && mask[c]) {
+      const int64_t o = wix<MT>(i, c);
+      const double rv = first ? b[i + c * ld] : b[i + c * ld] - q64[o];
+      r[o] = dd_of(rv);
+      acc[c] = fma(rv, rv, acc[c]);
+    }
+  write_partials<MT, double>(a.red, 3, m, acc, s);
+  if (!grid_sync(a.bar)) return false;
+  reduce_slot<MT>(a.red, 3, m, rr);
+  return true;
+}
+
+// Mode 0 in double-float (MMD_MIXED at level 0): the Chronopoulos-Gear CG of
+// cgcg with r, p, s = A p, w = A r and the iterate held as FP32 pairs and
+// the matrix as its pair copy; the scalars alpha, beta stay FP64.  When the
+// recurrence residual meets tol, x (FP64) is formed and its FP64 residual
+// b - A x is checked; a column above tol restarts CG from its current x with
+// that residual (at most three restarts, and only while the true residual
+// falls), else it stops unconverged (conv = 0) and the caller finishes it
+// in FP64.  On exit x holds the solution in FP64.
+template <int MT>
+__global__ void __launch_bounds__(threads_for<MT>(), 1) dd_cg_kernel(SolverArgs a) {
+  __shared__ Sh<MT> s;
+  __shared__ float2 s_ab[2 * MT];  // alpha, beta of the columns as pairs
+  __shared__ double s_true[MT], s_last[MT];
+  __shared__ long long s_base[MT];
+  grid_sync_init();
+  const double* __restrict__ b = (const double*)a.b;
+  double* __restrict__ x = (double*)a.x;
+  dd* const r = (dd*)a.r;
+  dd* const p = (dd*)a.p;
+  dd* const sv = (dd*)a.q;
+  dd* const w = (dd*)a.z;
+  dd* const xd = (dd*)a.ir;
+  float2* const red2 = (float2*)a.red;
+  const int m = a.m;
+  const int64_t n = a.n, ld = a.ld;
+  int all1[MT];
+#pragma unroll
+  for (int c = 0; c < MT; ++c) all1[c] = 1;
+  // iterate as pairs; ||b||
+  double acc[MT];
+#pragma unroll
+  for (int c = 0; c < MT; ++c) acc[c] = 0.0;
+  FOR_BLOCK_SHARE(i, n)
+    _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) {
+      const int64_t o = wix<MT>(i, c), ox = i + c * ld;
+      if (a.x0) {
+        xd[o] = dd_of(x[ox]);
+      } else {
+        xd[o] = {0.f, 0.f};
+        x[ox] = 0.0;
+      }
+      acc[c] = fma(b[ox], b[ox], acc[c]);
+    }
+  write_partials<MT, double>(a.red, 2, m, acc, s);
+  if (!grid_sync(a.bar)) return;
+  reduce_slot<MT>(a.red, 2, m, s.bn);
+  if (!dd_true_residual<MT>(a, s, all1, !a.x0, s_true)) return;
+  if (threadIdx.x < m) {
+    const int c = threadIdx.x;
+    s.bn[c] = sqrt(s.bn[c]);
+    s.rr[c] = s_true[c];
+    s.act[c] = (s.bn[c] > 0.0) && !(sqrt(s.rr[c]) <= a.tol * s.bn[c]);
+    s.ok[c] = !s.act[c];
+    s.it[c] = 0;
+    s_last[c] = sqrt(s.rr[c]);
+  }
+  __syncthreads();
+  for (int pass = 0;; ++pass) {
+    if (threadIdx.x < m) s_base[threadIdx.x] = s.it[threadIdx.x];
+    __syncthreads();
+    for (int it = 1;; ++it) {
+      int run[MT], any = 0;
+#pragma unroll
+      for (int c = 0; c < MT; ++c) {
+        run[c] = (c < m) && s.act[c] == 1;
+        any |= run[c];
+      }
+      if (!any) break;
+      // w = A r; delta = r^T w, gamma = r^T r
+      dd pa[MT], pb[MT];
+#pragma unroll
+      for (int c = 0; c < MT; ++c) pa[c] = pb[c] = {0.f, 0.f};
+      spmv_dd<MT>(a.A, r, w, m, run, r, pa, pb);
+      write_partials_dd<MT>(red2, 0, m, pa, 1, pb);
+      if (!grid_sync(a.bar)) return;
+      reduce_slot_dd<MT>(red2, 0, m, s.val, 1, s.val2);
+      if (threadIdx.x < m) {
+        const int c = threadIdx.x;
+        if (s.act[c] == 1) {
+          const double g = s.val2[c], dl = s.val[c];
+          if (it > 1 && g <= a.tol * a.tol * s.bn[c] * s.bn[c]) {
+            s.act[c] = 2;  // recurrence converged after update it - 1: check the true residual
+          } else if (s_base[c] + it <= a.maxit) {
+            double be = 0.0, den = dl;
+            if (it > 1) {
+              be = g / s.rz[c];
+              den = dl - be * g / s.alpha[c];
+            }
+            if (!(den > 0.0)) {  // not SPD at this precision: the caller finishes in FP64
+              s.act[c] = 0;
+            } else {
+              s.rz[c] = g;
+              s.alpha[c] = g / den;
+              const dd al = dd_of(s.alpha[c]), bt = dd_of(be);
+              s_ab[c] = make_float2(al.hi, al.lo);
+              s_ab[MT + c] = make_float2(bt.hi, bt.lo);
+              s.it[c] = s_base[c] + it;
+            }
+          } else {
+            s.act[c] = 0;  // iteration cap
+          }
+        }
+      }
+      __syncthreads();
+      int upd[MT];
+#pragma unroll
+      for (int c = 0; c < MT; ++c) upd[c] = (c < m) && s.act[c] == 1;
+      const bool first = (it == 1);
+      FOR_BLOCK_SHARE(i, n)
+        _Pragma("unroll") for (int c = 0; c < MT; ++c) if (upd[c]) {
+          const int64_t o = wix<MT>(i, c);
+          const dd al = {s_ab[c].x, s_ab[c].y}, be = {s_ab[MT + c].x, s_ab[MT + c].y};
+          const dd rv0 = r[o];
+          const dd pv = first ? rv0 : dd_fma(be, p[o], rv0);
+          const dd svv = first ? w[o] : dd_fma(be, sv[o], w[o]);
+          p[o] = pv;
+          sv[o] = svv;
+          xd[o] = dd_fma(al, pv, xd[o]);
+          r[o] = dd_fma(dd_neg(al), svv, rv0);
+        }
+      if (!grid_sync(a.bar)) return;
+      // columns whose recurrence converged leave the loop with act = 2
+      int more = 0;
+      _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) more |= (s.act[c] == 1);
+      if (!more) break;
+    }
+    // x = the pair iterate in FP64; true residual of the columns that converged in the recurrence
+    int chk[MT];
+#pragma unroll
+    for (int c = 0; c < MT; ++c) chk[c] = (c < m) && s.act[c] == 2;
+    FOR_BLOCK_SHARE(i, n)
+      _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) x[i + c * ld] = dd_val(xd[wix<MT>(i, c)]);
+    if (!grid_sync(a.bar)) return;
+    int anychk = 0;
+    _Pragma("unroll") for (int c = 0; c < MT; ++c) anychk |= chk[c];
+    if (!anychk) break;
+    if (!dd_true_residual<MT>(a, s, chk, false, s_true)) return;
+    if (threadIdx.x < m) {
+      const int c = threadIdx.x;
+      if (chk[c]) {
+        const double tn = sqrt(s_true[c]);
+        if (tn <= a.tol * s.bn[c]) {
+          s.act[c] = 0;
+          s.ok[c] = 1;
+        } else if (pass < 3 && tn < 0.5 * s_last[c]) {
+          s.act[c] = 1;  // restart from x with the true residual
+          s.rr[c] = s_true[c];
+          s_last[c] = tn;
+        } else {
+          s.act[c] = 0;  // stalled: reported unconverged
+        }
+      }
+    }
+    __syncthreads();
+    int again = 0;
+    _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) again |= (s.act[c] == 1);
+    if (!again) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < m) {
+    a.it_out[threadIdx.x] = s.it[threadIdx.x];
+    a.conv[threadIdx.x] = s.ok[threadIdx.x];
+  }
+}
+
+// VC = 1: the instance with the V-cycle (mode 3) and polynomial (mode 4)
+// preconditioners, kept apart so that the other modes' register allocation
+// does not see their calls.
 template <int MT, typename T, int VC>
 __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs a) {
   __shared__ Sh<MT> s;
@@ -839,13 +1272,13 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
   const int m = a.m;
   const int64_t n = a.n, ld = a.ld;
   if constexpr (VC == 1 && sizeof(T) == 8) {
-    if (a.mg_only) {  // one application z = V(b): b and x column-major, all m columns
+    if (a.mg_only) {  // one application z = V(b) or p(D^{-1}A) D^{-1} b: b and x column-major, all m columns
       FOR_BLOCK_SHARE(i, n)
         _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) r[wix<MT>(i, c)] = b[i + c * ld];
       if (threadIdx.x < MT) s.act[threadIdx.x] = threadIdx.x < m;
       __syncthreads();
       if (!grid_sync(a.bar)) return;
-      if (!mg_vcycle<MT>(a, s.act)) return;
+      if (!(a.mode == 4 ? cheb_prec<MT>(a, s.act) : mg_vcycle<MT>(a, s.act))) return;
       FOR_BLOCK_SHARE(i, n)
         _Pragma("unroll") for (int c = 0; c < MT; ++c) if (c < m) x[i + c * ld] = z[wix<MT>(i, c)];
       if (blockIdx.x == 0 && threadIdx.x < m) {
@@ -934,11 +1367,15 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
     return;
   }
   T* zv = r;
-  if (a.mode == 1 || a.mode == 3) {
+  if (a.mode == 1 || a.mode == 3 || a.mode == 4) {
     if (a.mode == 1) {
       if (!inner_cg<MT, T>(a, s)) return;
     } else if constexpr (sizeof(T) == 8 && VC == 1) {
-      if (!mg_vcycle<MT>(a, s.act)) return;
+      if (a.mode == 4) {
+        if (!cheb_prec<MT>(a, s.act)) return;
+      } else if (!mg_vcycle<MT>(a, s.act)) {
+        return;
+      }
     }
     zv = z;
 #pragma unroll
@@ -1026,7 +1463,7 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
       }
     }
     __syncthreads();
-    if (a.mode == 1 || a.mode == 3) {
+    if (a.mode == 1 || a.mode == 3 || a.mode == 4) {
       // columns that just converged (-1) need no preconditioning
       if (threadIdx.x < m) {
         const int c = threadIdx.x;
@@ -1037,7 +1474,11 @@ __global__ void __launch_bounds__(threads_for<MT>(), 1) solve_kernel(SolverArgs 
       if (a.mode == 1) {
         if (!inner_cg<MT, T>(a, s)) return;
       } else if constexpr (sizeof(T) == 8 && VC == 1) {
-        if (!mg_vcycle<MT>(a, s.act)) return;
+        if (a.mode == 4) {
+          if (!cheb_prec<MT>(a, s.act)) return;
+        } else if (!mg_vcycle<MT>(a, s.act)) {
+          return;
+        }
       }
 #pragma unroll
       for (int c = 0; c < MT; ++c) acc[c] = acc2[c] = T(0);
@@ -1101,6 +1542,30 @@ void allow_smem() {
   });
 }
 
+template <int MT>
+void allow_smem_dd() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(dd_cg_kernel<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem<MT>());
+  });
+}
+
+template <int MT>
+int max_blocks_dd() {
+  allow_smem_dd<MT>();
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dd_cg_kernel<MT>, threads_for<MT>(), dyn_smem<MT>());
+  return nb;
+}
+
+template <int MT>
+cudaError_t launch_dd(const SolverArgs& a, int grid, cudaStream_t st) {
+  allow_smem_dd<MT>();
+  void* args[] = {(void*)&a};
+  return cudaLaunchCooperativeKernel((const void*)dd_cg_kernel<MT>, dim3(grid), dim3(threads_for<MT>()), args,
+                                     dyn_smem<MT>(), st);
+}
+
 template <int MT, typename T, int VC>
 int max_blocks_for() {
   allow_smem<MT, T, VC>();
@@ -1123,17 +1588,27 @@ int solver_threads(int mt) { return mt == 1 ? threads_for<1>() : threads_for<4>(
 
 // One block per SM (the reductions read one partial per block, <= 1024).
 int solver_max_grid(int mt, int num_sms) {
-  const int nb = (mt == 1) ? std::min(std::min(max_blocks_for<1, double, 0>(), max_blocks_for<1, float, 0>()),
-                                     max_blocks_for<1, double, 1>())
-                           : std::min(std::min(max_blocks_for<4, double, 0>(), max_blocks_for<4, float, 0>()),
-                                      max_blocks_for<4, double, 1>());
+  const int nb = (mt == 1) ? std::min(std::min(std::min(max_blocks_for<1, double, 0>(), max_blocks_for<1, float, 0>()),
+                                              max_blocks_for<1, double, 1>()),
+                                     max_blocks_dd<1>())
+                           : std::min(std::min(std::min(max_blocks_for<4, double, 0>(), max_blocks_for<4, float, 0>()),
+                                               max_blocks_for<4, double, 1>()),
+                                      max_blocks_dd<4>());
   const int g = (nb >= 1) ? num_sms : 0;
   return g > kMaxThreads ? kMaxThreads : g;
 }
 
 cudaError_t launch_solver(const SolverArgs& a, int mt, int grid, cudaStream_t st) {
-  if (a.mode == 3) {  // V-cycle: FP64 outer iteration only
-    if (a.fp32 || !a.mg || a.mg_K < 1) return cudaErrorInvalidValue;
+  if (a.df) {  // double-float CG on A (mode 0)
+    if (a.mode != 0 || a.fp32 || !a.A.val2 || !a.b || !a.x) return cudaErrorInvalidValue;
+    if (mt == 1) return launch_dd<1>(a, grid, st);
+    if (mt == 4) return launch_dd<4>(a, grid, st);
+    return cudaErrorInvalidValue;
+  }
+  if (a.mode == 3 || a.mode == 4) {  // V-cycle or polynomial: FP64 outer iteration only
+    if (a.fp32) return cudaErrorInvalidValue;
+    if (a.mode == 3 && (!a.mg || a.mg_K < 1)) return cudaErrorInvalidValue;
+    if (a.mode == 4 && (a.poly.deg < 1 || a.poly.deg > 32 || !a.poly.dinv)) return cudaErrorInvalidValue;
     if (mt == 1) return launch_tpl<1, double, 1>(a, grid, st);
     if (mt == 4) return launch_tpl<4, double, 1>(a, grid, st);
   } else if (a.fp32) {

@@ -58,7 +58,8 @@ def test_iteration_caps_return_partial_results():
 
 
 @pytest.mark.parametrize("bad", [{"alpha": 0.0}, {"beta": -1.0}, {"c_r": 0}, {"max_cg_iter": 0},
-                                 {"timeout_s": 0.0}, {"precision": 7}, {"d": -2}])
+                                 {"timeout_s": 0.0}, {"precision": 7}, {"d": -2}, {"poly_op": 33},
+                                 {"poly_refine": -1}, {"poly_ratio": 1.0}, {"mg_op": 9}])
 def test_invalid_options_refused_by_every_entry_point(bad):
     pkg = _pkg()
     A = W.fd2d(10, seed=W.BASE_SEED + 72)

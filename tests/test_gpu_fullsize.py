@@ -52,3 +52,36 @@ def test_torus_knn_200k_matches_independent_reference():
     G = (V @ V.T).cpu().numpy()
     assert np.abs(G - np.eye(N)).max() <= 1e-10
     h.close()
+
+
+def test_fd2d_64_config_matches_dense():
+    """The 2D FD workload at its full size: -div(a grad u) on 64 x 64 cells,
+    a = 10^U(-2,2), Dirichlet (n = 4096, nnz = 20,224), N = 50 leftmost
+    eigenpairs to residual 1e-10 in FP64, against dense LAPACK (numpy eigh of
+    the whole matrix): eigenvalues within max(1e-9, 10 u ||A|| / lambda_i)
+    relative, cluster subspaces within cos >= 1 - 1e-12, residual <= tol."""
+    import paper_1804_03415_gb300 as pkg
+
+    A = W.fd2d(64, seed=W.BASE_SEED)
+    assert A.n == 4096 and A.nnz == 20224
+    N, tol = 50, 1e-10
+    h = pkg.MMD(A.rowptr, A.col, A.val)
+    lam, V, st = h.eig_leftmost(N, tol)
+    h.close()
+    ev, EV = np.linalg.eigh(A.dense())
+    nA = float(np.abs(A.dense()).sum(axis=1).max())
+    rtol = np.maximum(1e-9, 10 * np.finfo(np.float64).eps * nA / ev[:N])
+    rel = np.abs(lam - ev[:N]) / ev[:N]
+    assert np.all(rel <= rtol), (int(np.argmax(rel / rtol)), float(rel.max()))
+    assert st["n_converged"] == N and st["max_rel_residual"] <= tol
+    # eigenvectors as cluster subspaces (relative gap < 1e-6), a cluster cut by N skipped
+    i = 0
+    while i < N:
+        j = i + 1
+        while j < len(ev) and ev[j] - ev[j - 1] <= 1e-6 * ev[j]:
+            j += 1
+        if j <= N:
+            s = np.linalg.svd(V[:, i:j].T @ EV[:, i:j], compute_uv=False)
+            assert s.min() >= 1 - 1e-12, (i, j, float(s.min()))
+        i = j
+    assert np.abs(V.T @ V - np.eye(N)).max() <= 1e-10

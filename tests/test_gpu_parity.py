@@ -144,13 +144,14 @@ def test_level_op_matches_oracle(fd_case, k):
     h.close()
 
 
-@pytest.mark.parametrize("k,prec", [(0, 0), (1, 0), (1, 1), (0, 2)])
+@pytest.mark.parametrize("k,prec", [(0, 0), (1, 0), (1, 1), (0, 1), (0, 2)])
 def test_level_op_block_matches_exact(fd_case, k, prec):
     """Multi-right-hand-side OP (the refinement's solver tiles): 11 columns =
-    one full tile of 8 and a ragged tile of 3; FP64 (prec 0), FP32 PCG inside
-    FP64 refinement on a coarse level (1) and FP32 level-0 CG with FP64
-    reliable updates (2).  Each column must meet the same bound as the
-    single-vector OP."""
+    two full tiles of 4 and a ragged tile of 3, run concurrently; FP64 (prec
+    0), FP32 PCG inside FP64 refinement on a coarse level (1, k = 1),
+    double-float level-0 CG checked by its FP64 residual (1, k = 0) and FP32
+    level-0 CG with FP64 reliable updates (2).  Each column must meet the
+    same bound as the single-vector OP."""
     A, D = fd_case
     if k > D.K:
         pytest.skip("level absent")
@@ -376,4 +377,49 @@ def test_refinement_with_vcycle_matches_plain_cg():
     for lam, V in ((lam1, V1), (lam0, V0)):
         assert_eigpairs_match(lam, V, ref.lam, ref.V, lam_next=evall[N])
     assert st1["refine_pcg_iters"] < st0["refine_pcg_iters"], (st1["refine_pcg_iters"], st0["refine_pcg_iters"])
+    h.close()
+
+
+@pytest.mark.parametrize("m", [1, 4, 6])
+def test_poly_matches_oracle(m):
+    """One application of the level-0 polynomial preconditioner (16 Chebyshev
+    steps on [hi / 1000, hi], FP32 arithmetic on the device) against the
+    oracle's FP64 one (oracle/mg.py PolyPrec), column by column: relative
+    2-norm difference <= 1e-4 (FP32 rounding of each step, carried through
+    the three-term recurrence); tiles of 1 and 4 columns and a ragged tile
+    of 2."""
+    from oracle import mg as OMG
+
+    A = W.torus_knn(3000, seed=W.BASE_SEED + 12)
+    h = _handle(A, n_coarse=80)
+    R = np.random.default_rng(60 + m).standard_normal((m, A.n))
+    Z = torch.zeros((m, A.n), dtype=torch.float64, device="cuda")
+    h.level_poly(_dev(R), Z, deg=16, ratio=1000.0)
+    Zo = OMG.PolyPrec(A.to_scipy(), deg=16, ratio=1000.0)(R.T).T
+    Zg = Z.cpu().numpy()
+    for c in range(m):
+        err = np.linalg.norm(Zg[c] - Zo[c]) / np.linalg.norm(Zo[c])
+        assert err <= 1e-4, (c, err)
+    h.close()
+
+
+@pytest.mark.parametrize("name", ["fd2d_24", "torus_3000"])
+def test_eig_with_poly_preconditioner_matches_oracle(name):
+    """Level-0 OP and refinement solves by PCG with the polynomial
+    preconditioner (poly_op, poly_refine) reach the oracle's eigenpairs at
+    the FP64 path's tolerances, with fewer level-0 PCG iterations than plain
+    CG; so does MMD_IRLM_CG with poly_op."""
+    pkg = _pkg()
+    make, N, tol, nc = EIG_CASES[name]
+    A, ref, evall = _oracle_eig(name)
+    h = _handle(A, n_coarse=nc)
+    lam0, _, st0 = h.eig_leftmost(N, tol, mg_refine=0)
+    lam, V, st = h.eig_leftmost(N, tol, poly_op=16, poly_refine=16)
+    assert_eigpairs_match(lam, V, ref.lam, ref.V, lam_next=evall[N])
+    assert st["max_rel_residual"] <= 10 * tol
+    assert np.allclose(V.T @ V, np.eye(N), atol=1e-10)
+    assert st["pcg_iters"] < st0["pcg_iters"], (st["pcg_iters"], st0["pcg_iters"])
+    lam2, V2, st2 = h.eig_leftmost(N, tol, method=pkg.MMD_IRLM_CG, poly_op=12, poly_ratio=300.0)
+    assert_eigpairs_match(lam2, V2, ref.lam, ref.V, lam_next=evall[N])
+    assert st2["max_rel_residual"] <= 10 * tol
     h.close()

@@ -530,3 +530,39 @@ def test_vcycle_coarse_correction_symmetry_and_convergence():
     assert np.linalg.norm(x - xs) <= 1e-6 * np.linalg.norm(xs)
     _, it_cg, _ = S.cg(A.to_scipy(), b, tol=1e-10)
     assert it * 4 < it_cg, (it, it_cg)
+
+
+def test_polynomial_preconditioner_closed_form_and_pcg():
+    """The level-0 polynomial preconditioner z = p(D^{-1}A) D^{-1} r equals
+    (I - R(D^{-1}A)) A^{-1} r with R(t) = T_s((theta - t)/delta) / T_s(theta/delta)
+    on [hi / ratio, hi] (closed form through the eigendecomposition of
+    D^{-1/2} A D^{-1/2}, independent of the recurrence), is a symmetric
+    positive definite operator, and flexible PCG with it reaches the dense
+    solution of a 1e-6-shifted graph Laplacian to tol in fewer than a
+    fifth of plain CG's iterations."""
+    from oracle import mg as MG
+
+    A = W.torus_knn(1200, seed=W.BASE_SEED + 95)
+    As = A.to_scipy()
+    Ad = A.dense()
+    d = Ad.diagonal()
+    for deg, ratio in ((1, 30.0), (4, 300.0), (16, 1000.0)):
+        P = MG.PolyPrec(As, deg=deg, ratio=ratio)
+        hi, lo = P.hi, P.lo
+        theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+        w, Q = np.linalg.eigh(Ad / np.sqrt(np.outer(d, d)))
+        tpoly = np.cosh(deg * np.arccosh((theta - w) / delta + 0j)).real / np.cosh(deg * np.arccosh(theta / delta))
+        # D^{-1}A = D^{-1/2} Q w Q^T D^{1/2}: (I - R) A^{-1} = D^{-1/2} Q ((1 - R) / w) Q^T D^{-1/2}
+        Pexp = (Q * ((1.0 - tpoly) / w)) @ Q.T / np.sqrt(np.outer(d, d))
+        Pm = P(np.eye(A.n))
+        assert np.abs(Pm - Pexp).max() <= 1e-9 * np.abs(Pexp).max(), (deg, ratio)
+        assert np.abs(Pm - Pm.T).max() <= 1e-10 * np.abs(Pm).max()
+        assert np.linalg.eigvalsh(0.5 * (Pm + Pm.T))[0] > 0
+    b = np.random.default_rng(9).standard_normal(A.n)
+    x, it, ok = MG.mg_pcg(As, b, MG.PolyPrec(As, deg=16, ratio=1000.0), tol=1e-10)
+    assert ok
+    xs = np.linalg.solve(Ad, b)
+    assert np.linalg.norm(As @ x - b) <= 1e-10 * np.linalg.norm(b)
+    assert np.linalg.norm(x - xs) <= 1e-6 * np.linalg.norm(xs)
+    _, it_cg, _ = S.cg(As, b, tol=1e-10)
+    assert it * 5 < it_cg, (it, it_cg)
