@@ -435,7 +435,7 @@ def job_value(world: int, n_eig: int, steps: int, max_ms: float) -> float:
     return world * n_eig * steps / (max_ms / 1e3)
 
 
-def kernel_case(which: str):
+def kernel_case(which: str, streams: int = 8):
     """Small fixed launches for ncu captures: 'op' = three Operator OP solves on
     level 0 of the torus 200k workload (one solver launch each), 'block' =
     three 8-column OP solves there (two of the refinement's 4-column tiles each), 'eig' = one full
@@ -451,8 +451,17 @@ def kernel_case(which: str):
         h = G.MMD(A.rowptr, A.col, A.val, k_max=1)
         x = torch.rand(A.n, dtype=torch.float64, device="cuda")
         y = torch.empty_like(x)
-        its = [h.level_op(0, x, y, 1e-6) for _ in range(3)]
-        print(json.dumps({"kernel_case": "op", "iters": its}))
+        its, ms = [], []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            its.append(h.level_op(0, x, y, 1e-6))
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        print(json.dumps({"kernel_case": "op", "iters": its, "ms": ms,
+                          "us_per_iter": [1e3 * t / i for t, i in zip(ms, its)]}))
     elif which == "eig":
         A = W.torus_knn(WORKLOAD["n"], k=WORKLOAD["k"], seed=W.BASE_SEED + 1)
         h = G.MMD(A.rowptr, A.col, A.val)
@@ -476,6 +485,28 @@ def kernel_case(which: str):
         e1.record()
         torch.cuda.synchronize()
         print(json.dumps({"kernel_case": "vcycle", "ms_per_vcycle_4cols": e0.elapsed_time(e1) / 20}))
+    elif which == "batch":
+        # the batched workload: 64 random geometric graphs (sizes log-uniform 2k-50k, mean degree 8,
+        # unit weights, Laplacian + 1e-6 I), N = 20 leftmost eigenpairs each, tol 1e-8, one call
+        mats = W.rgg_batch()
+        t0 = time.perf_counter()
+        hs = [G.MMD(A.rowptr, A.col, A.val) for A in mats]
+        build_s = time.perf_counter() - t0
+        Ns = [20] * len(mats)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = G.eig_leftmost_batched(hs, Ns, 1e-8, streams=streams, allow_noconv=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        worst = max(r[2]["max_rel_residual"] for r in res)
+        conv = sum(r[2]["n_converged"] for r in res)
+        print(json.dumps({"kernel_case": "batch", "streams": streams, "problems": len(mats),
+                          "sum_n": int(sum(A.n for A in mats)),
+                          "build_s": build_s, "solve_s": dt, "eigenpairs_per_s": sum(Ns) / dt,
+                          "n_converged": conv, "worst_rel_residual": worst}))
+        for x in hs:
+            x.close()
+        return
     elif which == "block":
         A = W.torus_knn(WORKLOAD["n"], k=WORKLOAD["k"], seed=W.BASE_SEED + 1)
         h = G.MMD(A.rowptr, A.col, A.val, k_max=1)
@@ -512,13 +543,14 @@ def main():
                     help="Chebyshev degree of the V-cycle preconditioning the level-0 Lanczos OP solves (0: plain CG)")
     ap.add_argument("--budget-s", type=float, default=1500.0,
                     help="wall-clock budget of the run; optional legs are skipped past it")
-    ap.add_argument("--kernel-case", choices=["op", "block", "eig", "spmv", "vcycle"], default=None)
+    ap.add_argument("--kernel-case", choices=["op", "block", "eig", "spmv", "vcycle", "batch"], default=None)
+    ap.add_argument("--streams", type=int, default=8, help="concurrent streams of the batch kernel case")
     args = ap.parse_args()
     if args.oracle_worker:
         oracle_sample_worker(args.oracle_worker)
         return
     if args.kernel_case:
-        kernel_case(args.kernel_case)
+        kernel_case(args.kernel_case, args.streams)
         return
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

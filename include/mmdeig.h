@@ -307,6 +307,19 @@ int mmd_level_poly(mmd_handle* h, int m, const double* R, double* Z, int deg, do
 #define MMD_SPMV_VARIANTS 6
 int mmd_spmv_tuning(const mmd_handle* h, int k, int which, float* ms_per_variant);
 
+/* The solver autotuner: at mmd_build, for every level k < K that runs CG /
+ * PCG solves and both tile widths (mt = 1 or 4 columns), the library times
+ * 20 iterations of CG on A^(k) at each of MMD_TUNE_GRIDS candidate grids
+ * (2 ... 152 blocks of 1024 threads, those that are resident and leave at
+ * least 64 rows per block) and runs that level's solves on the fastest grid
+ * (capped by the SMs a batched call or a concurrent tile lane may use).
+ * Returns the chosen grid, writes the candidates to grids and their measured
+ * microseconds per iteration to us_per_iter (0 = not tried) unless NULL;
+ * MMD_EINVAL for a host-only handle, k outside [0, K) or mt not 1 / 4.  The
+ * paper has no counterpart (its solves run on one CPU core). */
+#define MMD_TUNE_GRIDS 8
+int mmd_solver_tuning(const mmd_handle* h, int k, int mt, int* grids, float* us_per_iter);
+
 void mmd_free(mmd_handle* h);
 const char* mmd_strerror(int code);
 const char* mmd_last_error(void);

@@ -139,6 +139,16 @@ class MMD:
             _lib.check(v, "mmd_spmv_tuning")
         return v, [float(x) for x in ms]
 
+    def solver_tuning(self, k=0, mt=1):
+        """(chosen solver grid, candidate grids, us per CG iteration of every
+        candidate, 0 = not tried) of level k for tiles of mt columns."""
+        g = (C.c_int * _lib.MMD_TUNE_GRIDS)()
+        us = (C.c_float * _lib.MMD_TUNE_GRIDS)()
+        v = self._lib.mmd_solver_tuning(self.h, k, mt, g, us)
+        if v < 0:
+            _lib.check(v, "mmd_solver_tuning")
+        return v, [int(x) for x in g], [float(x) for x in us]
+
     def level_vcycle(self, R, Z, deg=2, stream=0):
         """Z = V(R): one application of the level-0 V-cycle preconditioner;
         R, Z: CUDA float64 tensors (m, n), one row per column."""

@@ -90,6 +90,7 @@ SIGNATURES = {
     "mmd_spmv_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "mmd_level_vcycle": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "mmd_level_poly": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p]),
+    "mmd_solver_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "mmd_level_bsolve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                    C.POINTER(C.c_int64), C.c_void_p]),
     "mmd_free": (None, [C.c_void_p]),
@@ -101,6 +102,7 @@ SIGNATURES = {
 
 MMD_NOALLOC_MAX_N = 262144
 MMD_SPMV_VARIANTS = 6
+MMD_TUNE_GRIDS = 8
 
 _lib = None
 

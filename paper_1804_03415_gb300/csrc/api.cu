@@ -484,6 +484,7 @@ int mmd_build(const mmd_csr* A, const mmd_build_opts* opts, mmd_handle** out) {
     h->on_device = true;
     cudaGetDevice(&h->device);
     rc = upload_levels(h);
+    if (rc == MMD_OK) rc = tune_solver(h);
   }
   if (rc != MMD_OK) {
     mmd_free(h);
@@ -600,6 +601,19 @@ int mmd_spmv_tuning(const mmd_handle* h, int k, int which, float* ms_per_variant
   if (ms_per_variant)
     for (size_t v = 0; v < D.spmv_ms.size(); ++v) ms_per_variant[v] = D.spmv_ms[v];
   return D.spmv_variant;
+}
+
+int mmd_solver_tuning(const mmd_handle* h, int k, int mt, int* grids, float* us_per_iter) {
+  if (!h || !h->on_device || k < 0 || k >= (int)h->levels.size() || (mt != 1 && mt != 4)) {
+    set_error("mmd_solver_tuning: bad arguments (device handle, 0 <= k < K, mt 1 or 4)");
+    return MMD_EINVAL;
+  }
+  const int w = mt == 1 ? 0 : 1;
+  for (int i = 0; i < 8; ++i) {
+    if (grids) grids[i] = kTuneGrids[i];
+    if (us_per_iter) us_per_iter[i] = h->dl[k].grid_us[w][i];
+  }
+  return h->dl[k].grid[w];
 }
 
 int mmd_level_vcycle(mmd_handle* h, int m, const double* R, double* Z, int deg, void* stream) {

@@ -409,6 +409,7 @@ struct Ctx {
     a.mg_only = only;
   }
   int mg_deg = 2, mg_only = 0;
+  int force_grid = 0;  // the autotuner's trial grid (0: tuned or heuristic)
 
   // The polynomial preconditioner of level 0 (mode 4): Chebyshev coefficients
   // of degree deg on [hi / poly_ratio, hi] (hi: Gershgorin bound of D^{-1} A)
@@ -578,7 +579,9 @@ struct Ctx {
     const int MT = (m > 1) ? 4 : 1;
     // one block per 1024 rows (at least 16, at most one per SM): small levels
     // leave SMs free for other solves running concurrently on other streams
-    int grid = std::min(solver_max_grid(MT, ws->nsm), std::max(16, (int)((n + 1023) / 1024)));
+    const int tuned = L.grid[MT == 1 ? 0 : 1];
+    int grid = std::min(solver_max_grid(MT, ws->nsm),
+                        force_grid > 0 ? force_grid : tuned > 0 ? tuned : std::max(16, (int)((n + 1023) / 1024)));
     if (coop_grid_cap() > 0) grid = std::min(grid, coop_grid_cap());
     if (grid < 1) {
       set_error("solver kernel cannot be made resident");
@@ -1317,6 +1320,76 @@ int level_op_block(mmd_handle* h, int k, int m, const double* x, double* y, doub
       return MMD_ENOCONV;
     }
   } catch (const CudaFail& f) {
+    return f.code;
+  }
+  return MMD_OK;
+}
+
+// The solver autotuner: for every level that runs CG / PCG solves (k < K)
+// and both tile widths, 20 iterations of CG on A^(k) from a random
+// right-hand side (tolerance out of reach, so every trial runs the same
+// iterations) are timed with events at each candidate grid that is resident
+// and leaves at least 64 rows per block; the fastest grid is kept in the
+// level.  Runs once per handle, on a private stream, before any solve.
+int tune_solver(mmd_handle* h) {
+  cudaStream_t st = nullptr;
+  try {
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    mmd_eig_opts o;
+    mmd_default_eig_opts(&o);
+    Ctx c(h, st, o);
+    const int K = (int)h->levels.size();
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int k = 0; k < K; ++k) {
+      DLevel& L = h->dl[k];
+      const int64_t n = L.n;
+      for (int w = 0; w < 2; ++w) {
+        const int mt = w == 0 ? 1 : 4;
+        double* B = buf<double>(c.ws, "tn_b", size_t(n) * mt);
+        double* X = buf<double>(c.ws, "tn_x", size_t(n) * mt);
+        k_random(B, n * mt, 12345u, 77u + w, nullptr, st);
+        c.after_launch();
+        const int gmax = solver_max_grid(mt, c.ws->nsm);
+        float best = 0.f;
+        int bestg = 0;
+        bool warm = false;
+        for (int ci = 0; ci < 8; ++ci) {
+          const int g = std::min(kTuneGrids[ci], c.ws->nsm);
+          L.grid_us[w][ci] = 0.f;
+          if (g > gmax || (ci > 0 && int64_t(g) * 64 > n) || (ci > 0 && g == std::min(kTuneGrids[ci - 1], c.ws->nsm)))
+            continue;
+          c.force_grid = g;
+          std::vector<int64_t> its;
+          if (!warm) {  // first launch of this instance on this level: not timed
+            c.solve_raw(k, 0, false, B, X, mt, 0, 1e-300, 20, &its, nullptr, nullptr);
+            its.clear();
+            warm = true;
+          }
+          CK(cudaEventRecord(e0, st));
+          c.solve_raw(k, 0, false, B, X, mt, 0, 1e-300, 20, &its, nullptr, nullptr);
+          CK(cudaEventRecord(e1, st));
+          CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          const float us = 1e3f * ms / 21.f;  // 20 iterations + the closing product
+          L.grid_us[w][ci] = us;
+          if (bestg == 0 || us < best) {
+            best = us;
+            bestg = g;
+          }
+        }
+        L.grid[w] = bestg;
+      }
+    }
+    c.force_grid = 0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaStreamSynchronize(st));
+    cudaStreamDestroy(st);
+  } catch (const CudaFail& f) {
+    if (st) cudaStreamDestroy(st);
     return f.code;
   }
   return MMD_OK;

@@ -17,6 +17,9 @@ int level_op_block(mmd_handle* h, int k, int m, const double* x, double* y, doub
 int level_bsolve(mmd_handle* h, int k, const double* q, double* x, double tol, int max_iter, int64_t* iters,
                  cudaStream_t st);
 int level_vcycle(mmd_handle* h, int m, const double* R, double* Z, int deg, cudaStream_t st);
+// Candidate grids of the solver autotuner (blocks of 1024 threads, one per SM)
+constexpr int kTuneGrids[8] = {2, 4, 8, 16, 32, 64, 96, 152};
+int tune_solver(mmd_handle* h);
 int level_poly(mmd_handle* h, int m, const double* R, double* Z, int deg, double ratio, cudaStream_t st);
 int run_eig(mmd_handle* h, int N, double tol, const mmd_eig_opts& o, double* lambda, double* V, int outdev,
             mmd_eig_stats* stats);

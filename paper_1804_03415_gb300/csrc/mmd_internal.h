@@ -72,6 +72,11 @@ struct DLevel {
   float* dinv32 = nullptr;     // 1 / diag A^(k), k < K
   double gersh = 0;            // max_i sum_j |a_ij| / a_ii of A^(k), k < K
   float* kinv32 = nullptr;     // k = K: (A^(K))^{-1}, dense N^(K) x N^(K)
+  // grid of the persistent solver for tiles of 1 and 4 columns, chosen by the
+  // autotuner at build (0: not tuned, the size heuristic applies), with every
+  // candidate's measured time per CG iteration (us; 0: candidate not tried)
+  int grid[2] = {0, 0};
+  float grid_us[2][8] = {};
 };
 
 struct Workspace;

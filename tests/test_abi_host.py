@@ -117,6 +117,7 @@ def test_entry_points_refuse_host_only_handles_and_bad_options(pkg):
         pkg._lib.MMD_EINVAL
     g = np.zeros(A.nnz)
     assert lib.eig_grad(h.h, lam.ctypes.data, None, 0, g.ctypes.data, 0, C.byref(o)) == pkg._lib.MMD_EINVAL
+    assert lib.mmd_solver_tuning(h.h, 0, 1, None, None) == pkg._lib.MMD_EINVAL
     h.close()
     for bad in ({"peel": -1.0}, {"loc_radius": -1}, {"s_max": 0}):
         with pytest.raises(pkg.MMDError):

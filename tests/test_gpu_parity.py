@@ -423,3 +423,29 @@ def test_eig_with_poly_preconditioner_matches_oracle(name):
     assert_eigpairs_match(lam2, V2, ref.lam, ref.V, lam_next=evall[N])
     assert st2["max_rel_residual"] <= 10 * tol
     h.close()
+
+
+def test_solver_tuning_picks_the_fastest_tried_grid():
+    """The solver autotuner of mmd_build: on every level that runs solves
+    and for both tile widths it reports the candidates it timed (resident,
+    at least 64 rows per block, the smallest always tried) and the grid it
+    chose is the fastest of them; the coarsest level and bad tile widths
+    are refused."""
+    pkg = _pkg()
+    A = W.torus_knn(3000, seed=W.BASE_SEED + 12)
+    h = _handle(A, n_coarse=80)
+    K = h._lib.mmd_num_levels(h.h)
+    assert K >= 2
+    for k in range(K):
+        n = h._lib.mmd_level_size(h.h, k)
+        for mt in (1, 4):
+            g, cand, us = h.solver_tuning(k, mt)
+            tried = [(t, c) for t, c in zip(us, cand) if t > 0]
+            assert tried and us[0] > 0
+            assert all(c * 64 <= n or c == cand[0] for _, c in tried)
+            assert g == min(tried)[1], (k, mt, g, tried)
+    with pytest.raises(pkg.MMDError):
+        h.solver_tuning(K, 1)
+    with pytest.raises(pkg.MMDError):
+        h.solver_tuning(0, 2)
+    h.close()
