@@ -59,9 +59,10 @@ PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_all": 2}  # MMD_FP64, MMD_MIXED, MMD
 FP64_FMA_PER_CLK_SM = 1.68
 FP64_PEAK_TFLOPS = 152 * FP64_FMA_PER_CLK_SM * 2 * 2.070e9 / 1e12  # 1.057
 FP64_NOMINAL_TFLOPS = 1.25
-# DRAM bytes per launch of the solver from an ncu capture at the current kernel
-# (None until one is taken): reported as roofline.traffic
-TRAFFIC_PER_LAUNCH = None
+# DRAM bytes (read + write) per launch of the level-0 Operator OP kernel, solve_kernel<1, double, 0>,
+# from the ncu capture summarised in profiles/solve_kernel_op_torus_knn_200k_level0.md (32.63 MB read +
+# 0.81 MB written: the 30 MB level-0 matrix and the vectors once, every iteration after the first from L2)
+TRAFFIC_PER_LAUNCH = 33.44e6
 REF_EIGS = os.path.join(ROOT, "tests", "golden", "torus_knn_200k_eigs.json")
 
 
@@ -141,8 +142,9 @@ def oracle_sample_worker(steps: int):
     print(json.dumps({"times": times}))
 
 
-def run_oracle(steps: int) -> dict:
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+def run_oracle(steps: int, threads: int = 1) -> dict:
+    t = str(max(1, threads))
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t,
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", str(steps)],
                        capture_output=True, text=True, env=env, cwd=ROOT)
@@ -152,9 +154,10 @@ def run_oracle(steps: int) -> dict:
     return {"times": times, "value": SAMPLE["N"] / float(np.median(times))}
 
 
-def sample_desc():
-    return (f"oracle (numpy/scipy FP64, 1 thread): build + eig_leftmost N={SAMPLE['N']} tol={SAMPLE['tol']} "
-            f"on the same generator at {SAMPLE['npts']} points (a bounded sample of the 200k workload)")
+def sample_desc(threads: int = 1):
+    return (f"oracle (numpy/scipy FP64, BLAS/OpenMP threads limited to {threads}): build + eig_leftmost "
+            f"N={SAMPLE['N']} tol={SAMPLE['tol']} on the same generator at {SAMPLE['npts']} points (a bounded "
+            f"sample of the 200k workload)")
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -323,9 +326,16 @@ def gpu_arm(args, rank, world):
     pcg_bytes = sum(s["pcg_bytes"] for s in stats)
     pcg_flops = sum(s["pcg_flops"] for s in stats)
     pcg_launches = sum(s["pcg_launches"] for s in stats)
+    op_ms = sum(s["op0_ms"] for s in stats)
+    op_bytes = sum(s["op0_bytes"] for s in stats)
+    op_flops = sum(s["op0_flops"] for s in stats)
+    op_launches = sum(s["op0_launches"] for s in stats)
+    op_iters = sum(s["op0_iters"] for s in stats)
     peak, src = peaks()
     gbs = (pcg_bytes / (pcg_ms / 1e3) / 1e9) if pcg_ms > 0 else None
     tflops = (pcg_flops / (pcg_ms / 1e3) / 1e12) if pcg_ms > 0 else None
+    op_gbs = (op_bytes / (op_ms / 1e3) / 1e9) if op_ms > 0 else None
+    op_tflops = (op_flops / (op_ms / 1e3) / 1e12) if op_ms > 0 else None
     st0 = stats[-1]
     spmv = spmv_bench(G, W, torch, sptr, peak)
     out = {
@@ -347,19 +357,28 @@ def gpu_arm(args, rank, world):
         "e2e": {"value": world * N / e2e_s, "unit": "eigenpairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "includes": "mmd_build from host CSR + eig_leftmost to host, one run"},
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
-        "roofline": {"kernel": "solve_kernel (persistent CG/PCG)", "bound": "alu", "achieved": tflops,
-                     "peak": FP64_PEAK_TFLOPS,
+        "roofline": {"kernel": "solve_kernel<1, double, 0> (level-0 Operator OP: CG on A, one column)",
+                     "bound": "alu", "achieved": op_tflops, "peak": FP64_PEAK_TFLOPS,
                      "peak_source": "derived: 152 SMs x 1.68 FP64 FMA/clk/SM (measured on one SM) x 2 x 2.07 GHz; "
                                     f"nominal {FP64_NOMINAL_TFLOPS}",
-                     "unit": "TFLOP/s", "frac": (tflops / FP64_PEAK_TFLOPS) if tflops else None,
-                     "traffic": TRAFFIC_PER_LAUNCH, "launches": pcg_launches,
-                     "share_of_step": pcg_ms / max(ms_local, 1e-9),
-                     "note": "FP64 issue bound: the level matrices (30 MB at level 0) stay in L2 across "
-                             "iterations; algorithmic flops per column-iteration 2 nnz(A) + 10 n (+ 2 nnz(M) + 10 n "
-                             "per inner iteration)",
-                     "hbm_view": {"achieved": gbs, "peak": peak, "peak_source": src, "unit": "GB/s",
-                                  "frac": (gbs / peak) if gbs else None,
-                                  "bytes": "12 nnz + 4 n per iteration (matrix) + 72 n per column (vectors)"}},
+                     "unit": "TFLOP/s", "frac": (op_tflops / FP64_PEAK_TFLOPS) if op_tflops else None,
+                     "traffic": TRAFFIC_PER_LAUNCH if args.precision == "fp64" else None,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
+                                       "(profiles/solve_kernel_op_torus_knn_200k_level0.md)",
+                     "launches": op_launches, "iterations": op_iters,
+                     "algorithmic_flops_per_launch": (op_flops / op_launches) if op_launches else None,
+                     "share_of_step": op_ms / max(ms_local, 1e-9),
+                     "note": "latency bound (grid barriers, reduction rounds, L2 gathers of the SpMV): the 30 MB "
+                             "level-0 matrix stays in L2 across iterations; algorithmic flops per iteration "
+                             "2 nnz(A) + 10 n",
+                     "hbm_view": {"achieved": op_gbs, "peak": peak, "peak_source": src, "unit": "GB/s",
+                                  "frac": (op_gbs / peak) if op_gbs else None,
+                                  "bytes": "12 nnz + 4 n per iteration (matrix) + 72 n (vectors)"}},
+        "solver_all": {"kernel": "solve_kernel, every instance (OP, refinement tiles, coarse levels)",
+                       "achieved_tflops": tflops, "frac_of_fp64_peak": (tflops / FP64_PEAK_TFLOPS) if tflops else None,
+                       "achieved_gbs": gbs, "launches": pcg_launches, "share_of_step": pcg_ms / max(ms_local, 1e-9),
+                       "note": "the refinement's tiles run on four concurrent lanes, so their event-timed "
+                               "durations overlap"},
         "spmv": spmv,
         "clocks": clocks,
         "wall_s": time.perf_counter() - t_start,
@@ -557,7 +576,8 @@ def main():
         rank = int(os.environ.get("RANK", "0"))
         if rank != 0:
             return
-        o = run_oracle(args.warmup + args.steps)
+        nc = os.cpu_count() or 1
+        o = run_oracle(args.warmup + args.steps, nc)
         t = o["times"][args.warmup:]
         val = SAMPLE["N"] * len(t) / float(np.sum(t))
         line = {"impl": "reference", "metric": "leftmost eigenpairs/sec to residual 1e-8", "value": val,
@@ -568,8 +588,8 @@ def main():
                                sample=dict(SAMPLE, workload=f"torus_knn_{SAMPLE['npts']}",
                                            note="each step times the oracle on this bounded sample, not the "
                                                 "200k workload: the ratio to the GPU arm compares unlike sizes")),
-                "cpu_baseline": {"value": val, "unit": "eigenpairs/s", "cores": 1, "host_cores": os.cpu_count(),
-                                 "kind": "oracle", "sample": sample_desc()},
+                "cpu_baseline": {"value": val, "unit": "eigenpairs/s", "cores": nc, "host_cores": nc,
+                                 "kind": "oracle", "sample": sample_desc(nc)},
                 "e2e": {"value": val, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -577,12 +597,15 @@ def main():
     cpu = None
     rank0 = int(os.environ.get("RANK", "0")) == 0
     if rank0 and int(os.environ.get("WORLD_SIZE", "1")) == 1 and not args.no_cpu_baseline:
+        nc = os.cpu_count() or 1
         try:
-            o = run_oracle(1)
-            cpu = {"value": o["value"], "unit": "eigenpairs/s", "cores": 1, "host_cores": os.cpu_count(),
-                   "kind": "oracle", "sample": sample_desc()}
+            o = run_oracle(1, nc)
+            o1 = run_oracle(1, 1)
+            cpu = {"value": o["value"], "unit": "eigenpairs/s", "cores": nc, "host_cores": nc,
+                   "kind": "oracle", "sample": sample_desc(nc),
+                   "one_thread": {"value": o1["value"], "cores": 1, "sample": sample_desc(1)}}
         except Exception as e:  # reported, never silently replaced
-            cpu = {"value": None, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle", "error": str(e)[-300:]}
+            cpu = {"value": None, "unit": "eigenpairs/s", "cores": nc, "kind": "oracle", "error": str(e)[-300:]}
     rank, world = dist_init()
     out = gpu_arm(args, rank, world)
     out["cpu_baseline"] = cpu

@@ -159,6 +159,11 @@ typedef struct {
   double pcg_flops;     /* algorithmic floating-point operations of those launches */
   int64_t fp64_finishes; /* MMD_MIXED_ALL: level-0 CG columns FP32 left unconverged, finished in FP64 */
   double t_level_ms[16]; /* wall time per level k (coarsest solve; refinement + extension) */
+  /* profile == 1: the subset of those launches that are level-0 Operator OP solves (CG on A,
+     one column: the extension's Lanczos steps) */
+  int64_t op0_launches;
+  double op0_ms, op0_bytes, op0_flops;
+  int64_t op0_iters;
 } mmd_eig_stats;
 
 /* Read-only view of level k (1 <= k <= K) of a handle; host pointers owned by

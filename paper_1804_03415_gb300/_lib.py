@@ -50,7 +50,9 @@ class mmd_eig_stats(C.Structure):
                 ("max_rel_residual", C.c_double), ("mu1", C.c_double), ("t_total_ms", C.c_double),
                 ("pcg_launches", C.c_int64), ("pcg_ms", C.c_double), ("pcg_bytes", C.c_double),
                 ("pcg_flops", C.c_double),
-                ("fp64_finishes", C.c_int64), ("t_level_ms", C.c_double * 16)]
+                ("fp64_finishes", C.c_int64), ("t_level_ms", C.c_double * 16),
+                ("op0_launches", C.c_int64), ("op0_ms", C.c_double), ("op0_bytes", C.c_double),
+                ("op0_flops", C.c_double), ("op0_iters", C.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

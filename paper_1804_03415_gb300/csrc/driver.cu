@@ -710,6 +710,8 @@ struct Ctx {
     std::vector<int64_t> its;
     int64_t inner = 0;
     int nc = 0;
+    const int64_t l0 = S.pcg_launches;
+    const double ms0 = S.pcg_ms, by0 = S.pcg_bytes, fl0 = S.pcg_flops;
     if (k == 0 && o.poly_op > 0 && h->dl[0].dinv32) {
       // A^{-1} x by FP64 PCG preconditioned by a Chebyshev polynomial in D^{-1} A
       poly_deg = o.poly_op;
@@ -725,6 +727,13 @@ struct Ctx {
     }
     S.op_calls += 1;
     S.pcg_iters += its[0];
+    if (k == 0) {
+      S.op0_launches += S.pcg_launches - l0;
+      S.op0_ms += S.pcg_ms - ms0;
+      S.op0_bytes += S.pcg_bytes - by0;
+      S.op0_flops += S.pcg_flops - fl0;
+      S.op0_iters += its[0];
+    }
     S.inner_iters += inner;
     S.not_converged += nc;
     S.nc_solve += nc;
