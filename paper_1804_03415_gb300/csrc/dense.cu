@@ -198,7 +198,12 @@ __global__ void tri_apply_rot_kernel(int n, int p, int nsteps, const double* rc,
 // sweep to its rows of Z (Z <- Z G, full eigenvectors) when Z is given, and
 // thread 0 applies it to the row vector zl = e_{n-1}^T Z (last components,
 // the quantities of the Ritz estimate ||f|| |e_k^T y|) when zl is given.
-// On exit w holds the eigenvalues ascending and Z / zl are permuted alike.
+// The sweep is one chain of dependent FP64 operations, so it keeps what the
+// next rotation needs in registers (the running diagonal and off-diagonal
+// entries, zl's active entry) and forms each rotation from one reciprocal
+// square root; Z's rows carry their active entry in a register too, with the
+// next entry loaded ahead.  On exit w holds the eigenvalues ascending (ties
+// by position) and Z / zl are permuted alike.
 __global__ void tri_ql_kernel(const double* d_in, const double* e_in, int n, double* w, double* Z, int ldz,
                               double* zl, int* status) {
   extern __shared__ double sm[];
@@ -206,7 +211,7 @@ __global__ void tri_ql_kernel(const double* d_in, const double* e_in, int n, dou
   double* e = d + n;
   double* rc = e + n;
   double* rs = rc + n;
-  __shared__ int s_lo, s_hi, s_done;
+  __shared__ int s_lo, s_hi, s_done, s_nswap;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     d[k] = d_in[k];
     e[k] = (k < n - 1) ? e_in[k] : 0.0;
@@ -216,8 +221,8 @@ __global__ void tri_ql_kernel(const double* d_in, const double* e_in, int n, dou
       const int i = int(t % n), j = int(t / n);
       Z[i + size_t(j) * ldz] = (i == j) ? 1.0 : 0.0;
     }
-  if (zl && threadIdx.x == 0)
-    for (int k = 0; k < n; ++k) zl[k] = (k == n - 1) ? 1.0 : 0.0;
+  if (zl)
+    for (int k = threadIdx.x; k < n; k += blockDim.x) zl[k] = (k == n - 1) ? 1.0 : 0.0;
   __syncthreads();
   int hi = n - 1, iters = 0;
   const int max_iters = 40 * n + 100;
@@ -240,33 +245,42 @@ __global__ void tri_ql_kernel(const double* d_in, const double* e_in, int n, dou
         const double eh = e[hi - 1];
         const double den = dl + (dl >= 0 ? 1.0 : -1.0) * hypot(dl, eh);
         const double mu = d[hi] - ((den != 0.0) ? eh * eh / den : 0.0);
-        double x = d[lo] - mu, z = e[lo];
+        double a = d[lo], b = e[lo];  // d[k], e[k] as this rotation sees them
+        double x = a - mu, z = b;
+        double zk = zl ? zl[lo] : 0.0;
         for (int k = lo; k < hi; ++k) {
-          const double r = hypot(x, z);
-          double c = 1.0, s = 0.0;
-          if (r > 0.0) {
-            c = x / r;
-            s = z / r;
+          const double dd = d[k + 1];
+          const double e1 = (k < hi - 1) ? e[k + 1] : 0.0;
+          const double z1 = zl ? zl[k + 1] : 0.0;
+          const double r2 = fma(x, x, z * z);
+          double c = 1.0, sn = 0.0, r = 0.0;
+          if (r2 > 0.0) {
+            const double inv = rsqrt(r2);
+            c = x * inv;
+            sn = z * inv;
+            r = r2 * inv;
           }
           if (k > lo) e[k - 1] = r;
-          const double a = d[k], b = e[k], dd = d[k + 1];
-          const double cs = c * s, cc = c * c, ss = s * s;
+          const double cs = c * sn, cc = c * c, ss = sn * sn;
           d[k] = cc * a + 2 * cs * b + ss * dd;
-          d[k + 1] = ss * a - 2 * cs * b + cc * dd;
-          e[k] = cs * (dd - a) + (cc - ss) * b;
+          const double dk1 = ss * a - 2 * cs * b + cc * dd;
+          const double ek = cs * (dd - a) + (cc - ss) * b;
+          e[k] = ek;
           if (k < hi - 1) {
-            z = s * e[k + 1];
-            e[k + 1] = c * e[k + 1];
+            z = sn * e1;
+            b = c * e1;
           }
-          x = e[k];
+          x = ek;
+          a = dk1;
           rc[k] = c;
-          rs[k] = s;
+          rs[k] = sn;
           if (zl) {
-            const double a0 = zl[k], b0 = zl[k + 1];
-            zl[k] = c * a0 + s * b0;
-            zl[k + 1] = -s * a0 + c * b0;
+            zl[k] = c * zk + sn * z1;
+            zk = -sn * zk + c * z1;
           }
         }
+        d[hi] = a;
+        if (zl) zl[hi] = zk;
         s_lo = lo;
         s_hi = hi;
         ++iters;
@@ -276,47 +290,65 @@ __global__ void tri_ql_kernel(const double* d_in, const double* e_in, int n, dou
     if (s_done) break;
     if (Z) {
       const int lo = s_lo, h2 = s_hi;
-      for (int row = threadIdx.x; row < n; row += blockDim.x)
-        for (int k = lo; k < h2; ++k) {
-          double* q0 = Z + row + size_t(k) * ldz;
-          double* q1 = q0 + ldz;
-          const double a0 = *q0, b0 = *q1;
-          *q0 = rc[k] * a0 + rs[k] * b0;
-          *q1 = -rs[k] * a0 + rc[k] * b0;
-        }
-    }
-    __syncthreads();
-  }
-  // sort ascending (selection sort of the values; permutation applied to Z / zl)
-  __shared__ int s_i, s_j;
-  for (int i = 0; i < n - 1; ++i) {
-    if (threadIdx.x == 0) {
-      int m = i;
-      for (int j = i + 1; j < n; ++j)
-        if (d[j] < d[m]) m = j;
-      s_i = i;
-      s_j = m;
-      if (m != i) {
-        const double t = d[i];
-        d[i] = d[m];
-        d[m] = t;
-        if (zl) {
-          const double u = zl[i];
-          zl[i] = zl[m];
-          zl[m] = u;
-        }
-      }
-    }
-    __syncthreads();
-    if (Z && s_j != s_i)
       for (int row = threadIdx.x; row < n; row += blockDim.x) {
-        const double t = Z[row + size_t(s_i) * ldz];
-        Z[row + size_t(s_i) * ldz] = Z[row + size_t(s_j) * ldz];
-        Z[row + size_t(s_j) * ldz] = t;
+        double* q = Z + row;
+        double a0 = q[size_t(lo) * ldz], b0 = q[size_t(lo + 1) * ldz];
+        for (int k = lo; k < h2; ++k) {
+          const double bn = (k + 2 <= h2) ? q[size_t(k + 2) * ldz] : 0.0;
+          q[size_t(k) * ldz] = rc[k] * a0 + rs[k] * b0;
+          a0 = -rs[k] * a0 + rc[k] * b0;
+          b0 = bn;
+        }
+        q[size_t(h2) * ldz] = a0;
       }
+    }
     __syncthreads();
   }
-  for (int k = threadIdx.x; k < n; k += blockDim.x) w[k] = d[k];
+  // sort ascending: every thread ranks its entries (ties by position), the
+  // values and zl are scattered by rank, Z's columns permuted by the swaps
+  // thread 0 derives from the ranks (each thread swaps within its own rows)
+  int* rank = reinterpret_cast<int*>(rc);
+  int* swaps = reinterpret_cast<int*>(rs);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = d[i];
+    int r = 0;
+    for (int j = 0; j < n; ++j) r += (d[j] < v) || (d[j] == v && j < i);
+    rank[i] = r;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    w[rank[i]] = d[i];
+    if (zl) e[rank[i]] = zl[i];
+  }
+  __syncthreads();
+  if (zl)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) zl[i] = e[i];
+  if (Z) {
+    if (threadIdx.x == 0) {
+      // column i moves to rank[i]: swap i with its destination until i holds its own column
+      int ns = 0;
+      for (int i = 0; i < n; ++i)
+        while (rank[i] != i) {
+          const int j = rank[i];
+          swaps[2 * ns] = i;
+          swaps[2 * ns + 1] = j;
+          ++ns;
+          rank[i] = rank[j];
+          rank[j] = j;
+        }
+      s_nswap = ns;
+    }
+    __syncthreads();
+    const int ns = s_nswap;
+    for (int row = threadIdx.x; row < n; row += blockDim.x)
+      for (int t = 0; t < ns; ++t) {
+        double* p0 = Z + row + size_t(swaps[2 * t]) * ldz;
+        double* p1 = Z + row + size_t(swaps[2 * t + 1]) * ldz;
+        const double u = *p0;
+        *p0 = *p1;
+        *p1 = u;
+      }
+  }
 }
 
 // ------------------------------------------------------------ parallel Jacobi
@@ -585,7 +617,7 @@ void k_tri_ql(const double* d, const double* e, int n, double* w, double* Z, int
     cudaFuncSetAttribute(tri_ql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
   const size_t smem = sizeof(double) * 4 * size_t(n);
-  tri_ql_kernel<<<1, 256, smem, st>>>(d, e, n, w, Z, ldz, zl, status);
+  tri_ql_kernel<<<1, 512, smem, st>>>(d, e, n, w, Z, ldz, zl, status);
 }
 
 void k_tri_qr_sweeps(double* d, double* e, int n, const double* sh, int p, double* Q, int ldq, cudaStream_t st) {
