@@ -93,6 +93,10 @@ typedef struct {
   int threads;    /* host threads for the build, 0 = all cores */
   double peel;    /* > 0: split weakly attached rows off a patch while its 1/lambda_2
                      exceeds peel x the median over patches (bounds eps(P)); 0 = off */
+  int gpu_psi;    /* 1: with device = 1, the local psi solves of every level (Section 2.2's
+                     energy-minimising basis on each support, one dense KKT system per patch,
+                     independent across patches) run on the GPU, one block per patch; the
+                     integer indexing is the host's either way (default 1) */
 } mmd_build_opts;
 
 /* Solver options (Section 6 parameter rules). */

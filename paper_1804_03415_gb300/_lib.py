@@ -28,7 +28,8 @@ class mmd_csr(C.Structure):
 
 class mmd_build_opts(C.Structure):
     _fields_ = [("s_max", C.c_int), ("omega_max", C.c_int), ("loc_radius", C.c_int), ("n_coarse", C.c_int),
-                ("k_max", C.c_int), ("device", C.c_int), ("threads", C.c_int), ("peel", C.c_double)]
+                ("k_max", C.c_int), ("device", C.c_int), ("threads", C.c_int), ("peel", C.c_double),
+                ("gpu_psi", C.c_int)]
 
 
 class mmd_eig_opts(C.Structure):

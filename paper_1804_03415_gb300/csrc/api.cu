@@ -404,6 +404,7 @@ void mmd_default_build_opts(mmd_build_opts* o) {
   o->device = 1;
   o->threads = 0;
   o->peel = 0.0;
+  o->gpu_psi = 1;
 }
 
 void mmd_default_eig_opts(mmd_eig_opts* o) {
@@ -438,7 +439,8 @@ int mmd_build(const mmd_csr* A, const mmd_build_opts* opts, mmd_handle** out) {
   mmd_build_opts o;
   mmd_default_build_opts(&o);
   if (opts) o = *opts;
-  if (o.s_max < 1 || o.omega_max < 1 || o.n_coarse < 1 || o.k_max < 0 || o.loc_radius < 0 || !(o.peel >= 0)) {
+  if (o.s_max < 1 || o.omega_max < 1 || o.n_coarse < 1 || o.k_max < 0 || o.loc_radius < 0 || !(o.peel >= 0) ||
+      (o.gpu_psi != 0 && o.gpu_psi != 1)) {
     set_error("mmd_build: invalid build options");
     return MMD_EINVAL;
   }

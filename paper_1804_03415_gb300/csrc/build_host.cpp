@@ -18,6 +18,9 @@
 //      patterns, symmetrised.
 // Small dense problems use the routines below (cyclic Jacobi, Cholesky).
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -26,6 +29,7 @@
 #include <omp.h>
 #endif
 
+#include "build_gpu.h"
 #include "mmd_internal.h"
 
 namespace mmd {
@@ -756,15 +760,24 @@ int build_host(const mmd_csr* Ain, const mmd_build_opts* o, mmd_handle* h) {
   bool have_M = false;
   h->levels.clear();
   h->levels.reserve(o->k_max);
+  const char* dbg = getenv("MMD_DEBUG");
+  const bool debug = dbg && dbg[0] && dbg[0] != '0';
+  auto now = [] { return std::chrono::steady_clock::now(); };
+  auto ms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+  };
   while (cur->nrows > o->n_coarse && (int)h->levels.size() < o->k_max) {
     HLevel L;
     L.n_fine = cur->nrows;
+    const auto t0 = now();
     partition(*cur, o->s_max, L.patch_of, L.patch_ptr, L.patch_rows);
     peel_patches(*cur, o->peel, L.patch_of, L.patch_ptr, L.patch_rows, nt);
     L.n = (int64_t)L.patch_ptr.size() - 1;
     if (L.n >= cur->nrows) break;
     bool ok = true;
+    const auto t1 = now();
     local_bases(*cur, L.patch_ptr, L.patch_rows, L.patch_of, L.phi, L.uhat, L.eps, L.delta, L.used_closed, ok, nt);
+    const auto t2 = now();
     if (!ok) {
       set_error("mmd_build: a patch matrix A[S,S] is not positive definite at level " +
                 std::to_string(h->levels.size() + 1));
@@ -775,12 +788,23 @@ int build_host(const mmd_csr* Ain, const mmd_build_opts* o, mmd_handle* h) {
     const int radius = h->levels.empty() ? o->loc_radius : std::min(o->loc_radius, 1);
     neighbourhoods(*cur, L.patch_of, L.patch_ptr, L.patch_rows, o->omega_max, radius, L.omega_ptr, L.omega_rows,
                    nt);
+    const auto t3 = now();
     std::vector<double> psival;
-    if (!localized_psi(*cur, L.patch_of, L.phi, L.patch_rows, L.omega_ptr, L.omega_rows, L.n, psival, nt)) {
+    if (o->device && o->gpu_psi) {
+      std::vector<double> phi_of_row(cur->nrows);
+      for (int64_t x = 0; x < cur->nrows; ++x) phi_of_row[L.patch_rows[x]] = L.phi[x];
+      std::string err;
+      const int g = psi_solves_gpu(*cur, L.patch_of, phi_of_row, L.omega_ptr, L.omega_rows, L.n, psival, err);
+      if (g != 0) {
+        set_error("mmd_build: " + err + " at level " + std::to_string(h->levels.size() + 1));
+        return g > 0 ? MMD_ENOTSPD : MMD_ECUDA;
+      }
+    } else if (!localized_psi(*cur, L.patch_of, L.phi, L.patch_rows, L.omega_ptr, L.omega_rows, L.n, psival, nt)) {
       set_error("mmd_build: a neighbourhood matrix is not positive definite at level " +
                 std::to_string(h->levels.size() + 1));
       return MMD_ENOTSPD;
     }
+    const auto t4 = now();
     psi_to_csr(L.n_fine, L.n, L.omega_ptr, L.omega_rows, psival, L.psi);
     HCSR PsiT, T;
     transpose(L.psi, PsiT);
@@ -796,6 +820,12 @@ int build_host(const mmd_csr* Ain, const mmd_build_opts* o, mmd_handle* h) {
     }
     symmetrise(L.M);
     have_M = true;
+    if (debug)
+      fprintf(stderr,
+              "[mmd] build level %zu: n %lld -> %lld, partition %.1f ms, bases %.1f ms, supports %.1f ms, "
+              "psi %.1f ms, Galerkin %.1f ms (omega rows %zu)\n",
+              h->levels.size() + 1, (long long)L.n_fine, (long long)L.n, ms(t0, t1), ms(t1, t2), ms(t2, t3),
+              ms(t3, t4), ms(t4, now()), L.omega_rows.size());
     h->levels.push_back(std::move(L));
     cur = &h->levels.back().A;
   }

@@ -449,3 +449,30 @@ def test_solver_tuning_picks_the_fastest_tried_grid():
     with pytest.raises(pkg.MMDError):
         h.solver_tuning(0, 2)
     h.close()
+
+
+@pytest.mark.parametrize("case,rings,peel", [("torus_4000", 1, 0.0), ("torus_4000", 2, 3.0), ("fd2d_32", 3, 0.0),
+                                             ("rgg_3000", 1, 0.0)])
+def test_gpu_psi_build_matches_host_build(case, rings, peel):
+    """mmd_build with the local psi solves on the GPU (one block per patch,
+    the default for device handles) against the host build of the same
+    matrix: integer indexing bit for bit at every level, Psi, A^(k), M^(k)
+    values and eps, delta to 1e-10 relative (the same local KKT systems,
+    factorised in a different order)."""
+    A = {"fd2d_32": lambda: W.fd2d(32, seed=3), "torus_4000": lambda: W.torus_knn(4000, seed=4),
+         "rgg_3000": lambda: W.rgg(3000, seed=5)}[case]()
+    om = 256 if rings == 1 else 1024
+    kw = dict(n_coarse=50, peel=peel, loc_radius=rings, omega_max=om)
+    hg = _handle(A, **kw)
+    hh = _handle(A, device=False, **kw)
+    assert hg.num_levels == hh.num_levels >= 1
+    for k in range(1, hh.num_levels + 1):
+        G, H = hg.level(k), hh.level(k)
+        for f in ["patch_of", "patch_ptr", "patch_rows", "omega_ptr", "omega_rows"]:
+            assert np.array_equal(G[f], H[f]), (k, f)
+        for nm in ("A", "M", "psi"):
+            assert np.array_equal(G[nm][0], H[nm][0]) and np.array_equal(G[nm][1], H[nm][1]), (k, nm)
+            assert np.abs(G[nm][2] - H[nm][2]).max() <= 1e-10 * np.abs(H[nm][2]).max(), (k, nm)
+        assert abs(G["eps"] - H["eps"]) <= 1e-10 * H["eps"] and abs(G["delta"] - H["delta"]) <= 1e-10 * H["delta"]
+    hg.close()
+    hh.close()
