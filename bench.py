@@ -526,6 +526,30 @@ def kernel_case(which: str, streams: int = 8):
         for x in hs:
             x.close()
         return
+    elif which == "alpha":
+        # Section 7's alpha sweep: beta = 1, alpha in [3, 5], on the paper-shaped SwissRoll point cloud
+        # (20,000 points, kNN k = 10, weights exp(-r^2 / 0.1)); per level the most iterations one PCG
+        # call on A^(k) took, alone and over log(1 / eps^(k)) with eps^(k) the level's PCG tolerance
+        A = W.swissroll(20_000)
+        h = G.MMD(A.rowptr, A.col, A.val)
+        K = h.num_levels
+        eps = [h.level(k)["eps"] for k in range(1, K + 1)]
+        rows = []
+        for alpha in (3.0, 3.5, 4.0, 4.5, 5.0):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = h.eig_leftmost(500, 1e-8, alpha=alpha, beta=1.0, allow_noconv=True)[2]
+            torch.cuda.synchronize()
+            mu1 = st["mu1"]
+            # the PCG tolerance of level k >= 1 is 0.1 eps_k / mu_1 (relative), level 0 0.1 tol
+            tol_k = [1e-9] + [min(0.1, max(1e-14, 0.1 * e / mu1)) for e in eps[:-1]]
+            mx = st["max_pcg_iters"]
+            rows.append({"alpha": alpha, "s": time.perf_counter() - t0, "max_pcg_iters": mx,
+                         "max_pcg_iters_over_log": [m / np.log(1.0 / t) if t < 1 else None for m, t in zip(mx, tol_k)],
+                         "n_converged": st["n_converged"], "refine_iters": st["refine_iters"],
+                         "lanczos_steps": st["lanczos_steps"]})
+        print(json.dumps({"kernel_case": "alpha", "workload": "swissroll_20k", "levels": K, "eps": eps,
+                          "rows": rows}))
     elif which == "block":
         A = W.torus_knn(WORKLOAD["n"], k=WORKLOAD["k"], seed=W.BASE_SEED + 1)
         h = G.MMD(A.rowptr, A.col, A.val, k_max=1)
@@ -562,7 +586,7 @@ def main():
                     help="Chebyshev degree of the V-cycle preconditioning the level-0 Lanczos OP solves (0: plain CG)")
     ap.add_argument("--budget-s", type=float, default=1500.0,
                     help="wall-clock budget of the run; optional legs are skipped past it")
-    ap.add_argument("--kernel-case", choices=["op", "block", "eig", "spmv", "vcycle", "batch"], default=None)
+    ap.add_argument("--kernel-case", choices=["op", "block", "eig", "spmv", "vcycle", "batch", "alpha"], default=None)
     ap.add_argument("--streams", type=int, default=8, help="concurrent streams of the batch kernel case")
     args = ap.parse_args()
     if args.oracle_worker:

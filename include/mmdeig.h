@@ -168,6 +168,9 @@ typedef struct {
   int64_t op0_launches;
   double op0_ms, op0_bytes, op0_flops;
   int64_t op0_iters;
+  /* per level k: the most iterations one PCG call on A^(k) took (the extension's Operator OP
+     and the refinement's warm-started solves; Section 7's #^(A^(k))) */
+  int64_t max_pcg_iters[16];
 } mmd_eig_stats;
 
 /* Read-only view of level k (1 <= k <= K) of a handle; host pointers owned by

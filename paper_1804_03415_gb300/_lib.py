@@ -53,11 +53,12 @@ class mmd_eig_stats(C.Structure):
                 ("pcg_flops", C.c_double),
                 ("fp64_finishes", C.c_int64), ("t_level_ms", C.c_double * 16),
                 ("op0_launches", C.c_int64), ("op0_ms", C.c_double), ("op0_bytes", C.c_double),
-                ("op0_flops", C.c_double), ("op0_iters", C.c_int64)]
+                ("op0_flops", C.c_double), ("op0_iters", C.c_int64), ("max_pcg_iters", C.c_int64 * 16)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
         d["t_level_ms"] = [float(v) for v in self.t_level_ms[: max(self.n_levels, 0)]]
+        d["max_pcg_iters"] = [int(v) for v in self.max_pcg_iters[: max(self.n_levels, 0)]]
         return d
 
 

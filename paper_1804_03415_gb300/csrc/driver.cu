@@ -727,6 +727,7 @@ struct Ctx {
     }
     S.op_calls += 1;
     S.pcg_iters += its[0];
+    if (k < 16) S.max_pcg_iters[k] = std::max(S.max_pcg_iters[k], its[0]);
     if (k == 0) {
       S.op0_launches += S.pcg_launches - l0;
       S.op0_ms += S.pcg_ms - ms0;
@@ -1112,7 +1113,10 @@ int refine(Ctx& c, int k, double* Q0, std::vector<double>& D, double tol_rel, do
         c.solve(k, k == 0 ? 0 : 1, W, F, m, 1, tol_rel, c.o.max_cg_iter, &its, &inner, &nc);
       }
       c.S.refine_pcg_calls += m;
-      for (auto t : its) c.S.refine_pcg_iters += t;
+      for (auto t : its) {
+        c.S.refine_pcg_iters += t;
+        if (k < 16) c.S.max_pcg_iters[k] = std::max(c.S.max_pcg_iters[k], t);
+      }
       c.S.inner_iters += inner;
       c.S.not_converged += nc;
       c.S.nc_solve += nc;

@@ -476,3 +476,19 @@ def test_gpu_psi_build_matches_host_build(case, rings, peel):
         assert abs(G["eps"] - H["eps"]) <= 1e-10 * H["eps"] and abs(G["delta"] - H["delta"]) <= 1e-10 * H["delta"]
     hg.close()
     hh.close()
+
+
+def test_per_level_max_pcg_counters():
+    """stats.max_pcg_iters[k] (Section 7's largest iteration count of one PCG
+    call on A^(k)) is at least the mean over the level-0 OP calls, at most the
+    iteration cap, and zero on the dense coarsest level."""
+    make, N, tol, nc = EIG_CASES["torus_3000"]
+    A = make()
+    h = _handle(A, n_coarse=nc)
+    lam, V, st = h.eig_leftmost(N, tol, profile=1)
+    mx = st["max_pcg_iters"]
+    K = st["n_levels"] - 1
+    assert len(mx) == K + 1 and mx[K] == 0
+    assert all(0 < m <= 20000 for m in mx[:K])
+    assert mx[0] * st["op0_launches"] >= st["op0_iters"] > 0
+    h.close()
