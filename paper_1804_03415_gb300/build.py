@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmmdeig.so")
 OBJ = os.path.join(HERE, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["solver.cu", "blas.cu", "dense.cu", "driver.cu", "api.cu", "build_host.cpp", "build_gpu.cu", "noalloc.cu"]
+SOURCES = ["solver.cu", "blas.cu", "dense.cu", "driver.cu", "api.cu", "build_host.cpp", "build_gpu.cu", "wide.cu", "noalloc.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 

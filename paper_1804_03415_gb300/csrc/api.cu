@@ -130,6 +130,12 @@ static int upload_csr(const HCSR& A, DCSR& D) {
   if ((rc = dput(&D.val, A.val))) return rc;
   std::vector<float> v32(A.val.begin(), A.val.end());
   if ((rc = dput(&D.val32, v32))) return rc;
+  std::vector<float> v2(2 * A.val.size());
+  for (size_t i = 0; i < A.val.size(); ++i) {
+    v2[2 * i] = v32[i];
+    v2[2 * i + 1] = (float)(A.val[i] - (double)v32[i]);
+  }
+  if ((rc = dput(&D.val2, v2))) return rc;
   D.mean_row = A.nrows ? double(D.nnz) / double(A.nrows) : 0.0;
   int mx = 0;
   for (int64_t i = 0; i < A.nrows; ++i) mx = std::max(mx, A.rowptr[i + 1] - A.rowptr[i]);
@@ -278,6 +284,7 @@ static void free_csr(DCSR& D) {
   cudaFree(D.col);
   cudaFree(D.val);
   cudaFree(D.val32);
+  cudaFree(D.val2);
   cudaFree(D.s_ptr);
   cudaFree(D.s_len);
   cudaFree(D.s_row);

@@ -261,13 +261,94 @@ struct Ctx {
   // is accepted; columns it leaves unconverged continue in FP64 CG from
   // their current x.
   bool use_df = false;
+  // m >= 8 columns: all of them in one launch of the wide kernel per slice of
+  // up to kWideMaxCols columns (row-major pair vectors, coalesced row gathers)
+  void solve_wide(const double* B, double* X, int m, int x0, double tol, int maxit, std::vector<int64_t>& its,
+                  std::vector<int>& cv) {
+    const DLevel& L = h->dl[0];
+    const int64_t n = L.n;
+    const int grid = wide_max_grid(ws->nsm);
+    if (grid < 1) {
+      set_error("the wide solver kernel cannot be made resident");
+      throw CudaFail{MMD_ECUDA};
+    }
+    its.assign(m, 0);
+    cv.assign(m, 0);
+    for (int c0 = 0; c0 < m; c0 += kWideMaxCols) {
+      const int mc = std::min(kWideMaxCols, m - c0);
+      WideArgs a;
+      std::memset(&a, 0, sizeof(a));
+      a.n = n;
+      a.m = mc;
+      a.ld = n;
+      a.rowptr = L.A.rowptr;
+      a.col = L.A.col;
+      a.val2 = reinterpret_cast<const float2*>(L.A.val2);
+      a.val = L.A.val;
+      a.b = B + size_t(c0) * n;
+      a.x = X + size_t(c0) * n;
+      a.x0 = x0;
+      const size_t nm = size_t(n) * mc;
+      a.r = buf<double>(ws, "wd_r", nm);
+      a.p = buf<double>(ws, "wd_p", nm);
+      a.s = buf<double>(ws, "wd_s", nm);
+      a.w = buf<double>(ws, "wd_w", nm);
+      a.xd = buf<double>(ws, "wd_x", nm);
+      a.q64 = buf<double>(ws, "wd_q", nm);
+      a.red = buf<double>(ws, "wd_red", size_t(2) * mc * grid);
+      a.red64 = buf<double>(ws, "wd_red64", size_t(2) * mc * grid);
+      a.tol = tol;
+      a.maxit = maxit;
+      a.it_out = buf<int64_t>(ws, "wd_it", mc);
+      a.conv = buf<int>(ws, "wd_cv", mc);
+      unsigned* bar = buf<unsigned>(ws, "wd_bar", 64);
+      a.bar.count = bar;
+      a.bar.gen = bar + 32;
+      a.bar.status = ws->status;
+      a.bar.timeout_ns = (long long)timeout_ns;
+      CK(cudaMemsetAsync(bar, 0, sizeof(unsigned) * 64, st));
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (o.profile) {
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, st));
+      }
+      CK(launch_wide_cg(a, grid, st));
+      after_launch();
+      if (o.profile) CK(cudaEventRecord(e1, st));
+      CK(cudaMemcpyAsync(its.data() + c0, a.it_out, sizeof(int64_t) * mc, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(cv.data() + c0, a.conv, sizeof(int) * mc, cudaMemcpyDeviceToHost, st));
+      check_status();
+      if (o.profile) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        int64_t itsum = 0, itmax = 0;
+        for (int c = c0; c < c0 + mc; ++c) {
+          itsum += its[c];
+          itmax = std::max(itmax, its[c]);
+        }
+        const double zA = (double)L.A.nnz, nn = (double)n;
+        S.pcg_launches += 1;
+        S.pcg_ms += ms;
+        S.pcg_bytes += itmax * (12.0 * zA + 4.0 * nn) + itsum * 72.0 * nn;
+        S.pcg_flops += (double)itsum * (2.0 * zA + 10.0 * nn);
+      }
+    }
+  }
+
   void solve_df(const double* B, double* X, int m, int x0, double tol, int maxit, std::vector<int64_t>* iters,
                 int64_t* inner_total, int* notconv) {
     std::vector<int64_t> its;
     std::vector<int> cv;
-    use_df = true;
-    solve_raw(0, 0, false, B, X, m, x0, tol, maxit, &its, inner_total, nullptr, nullptr, nullptr, &cv);
-    use_df = false;
+    if (m >= 8 && h->dl[0].A.val2) {
+      solve_wide(B, X, m, x0, tol, maxit, its, cv);
+    } else {
+      use_df = true;
+      solve_raw(0, 0, false, B, X, m, x0, tol, maxit, &its, inner_total, nullptr, nullptr, nullptr, &cv);
+      use_df = false;
+    }
     const int64_t n = h->dl[0].n;
     for (int c = 0; c < m; ++c) {
       if (!cv[c]) {

@@ -99,6 +99,33 @@ struct SolverArgs {
   PolyPrec poly;  // mode 4
 };
 
+// Many right-hand sides of one level-0 solve (CG on A, the refinement's
+// block) in one persistent launch, double-float arithmetic (wide.cu).
+constexpr int kWideMaxCols = 128;
+struct WideArgs {
+  int64_t n;
+  int m;                    // columns, 1 .. kWideMaxCols
+  int64_t ld;               // leading dimension of b and x
+  const int32_t* rowptr;    // A (CSR, device order)
+  const int32_t* col;
+  const float2* val2;       // values as FP32 pairs
+  const double* val;        // values in FP64 (the residual check)
+  const double* b;          // n x m column-major, FP64
+  double* x;                // n x m column-major, FP64 (x0 on entry when x0)
+  int x0;
+  void *r, *p, *s, *w, *xd; // n x m row-major pairs (8 bytes each)
+  double* q64;              // n x m row-major FP64
+  void* red;                // [2][m][grid] float2 partials
+  double* red64;            // [2][m][grid] FP64 partials
+  double tol;
+  int maxit;
+  int64_t* it_out;          // m
+  int* conv;                // m
+  GridBarrier bar;
+};
+int wide_max_grid(int num_sms);
+cudaError_t launch_wide_cg(const WideArgs& a, int grid, cudaStream_t st);
+
 int solver_threads(int mt);
 int solver_max_grid(int mt, int num_sms);
 cudaError_t launch_solver(const SolverArgs& a, int mt, int grid, cudaStream_t st);

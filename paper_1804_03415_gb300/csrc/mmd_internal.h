@@ -36,6 +36,7 @@ struct DCSR {
   int32_t* col = nullptr;
   double* val = nullptr;
   float* val32 = nullptr;
+  float* val2 = nullptr;     // 2 x nnz: each CSR value as the FP32 pair (hi, lo), value = hi + lo
   double mean_row = 0;
   int max_row = 0;
   int64_t nslices = 0, sell_nnz = 0;

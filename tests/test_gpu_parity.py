@@ -492,3 +492,19 @@ def test_per_level_max_pcg_counters():
     assert all(0 < m <= 20000 for m in mx[:K])
     assert mx[0] * st["op0_launches"] >= st["op0_iters"] > 0
     h.close()
+
+
+@pytest.mark.parametrize("name", ["torus_3000", "rgg_2500"])
+def test_mixed_wide_refinement_matches_oracle(name):
+    """MMD_MIXED with plain CG in the level-0 refinement (mg_refine = 0): its
+    warm-started block of solves runs in the wide double-float kernel (all
+    columns in one launch, FP64 residual check) and the eigenpairs match the
+    oracle's at the FP64 path's tolerances."""
+    make, N, tol, nc = EIG_CASES[name]
+    A, ref, evall = _oracle_eig(name)
+    h = _handle(A, n_coarse=nc)
+    lam, V, st = h.eig_leftmost(N, tol, precision=1, mg_refine=0)
+    assert_eigpairs_match(lam, V, ref.lam, ref.V, lam_next=evall[N])
+    assert st["max_rel_residual"] <= 10 * tol
+    assert np.allclose(V.T @ V, np.eye(N), atol=1e-10)
+    h.close()
