@@ -171,6 +171,9 @@ typedef struct {
   /* per level k: the most iterations one PCG call on A^(k) took (the extension's Operator OP
      and the refinement's warm-started solves; Section 7's #^(A^(k))) */
   int64_t max_pcg_iters[16];
+  /* launches of the wide multi-column solve (MMD_MIXED, level-0 blocks of >= 8 columns) replayed
+     from the CUDA graph captured at its first call with the same buffers */
+  int64_t graph_replays;
 } mmd_eig_stats;
 
 /* Read-only view of level k (1 <= k <= K) of a handle; host pointers owned by

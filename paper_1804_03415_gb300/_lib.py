@@ -53,7 +53,8 @@ class mmd_eig_stats(C.Structure):
                 ("pcg_flops", C.c_double),
                 ("fp64_finishes", C.c_int64), ("t_level_ms", C.c_double * 16),
                 ("op0_launches", C.c_int64), ("op0_ms", C.c_double), ("op0_bytes", C.c_double),
-                ("op0_flops", C.c_double), ("op0_iters", C.c_int64), ("max_pcg_iters", C.c_int64 * 16)]
+                ("op0_flops", C.c_double), ("op0_iters", C.c_int64), ("max_pcg_iters", C.c_int64 * 16),
+                ("graph_replays", C.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

@@ -60,7 +60,19 @@ struct Workspace {
   // concurrent tiles of one multi-column solve: side streams and fork / join events
   cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t fork = nullptr, join[4] = {nullptr, nullptr, nullptr, nullptr};
+  // the wide multi-column launch captured in CUDA graphs, each with the
+  // arguments it was captured for (the refinement alternates between two
+  // buffer sets), replayed while they are unchanged; the oldest is replaced
+  static constexpr int kWideGraphs = 4;
+  cudaGraphExec_t wide_exec[kWideGraphs] = {};
+  WideArgs wide_key[kWideGraphs] = {};
+  int wide_next = 0;
+  bool wide_graph_off = false;  // capture failed once: launch directly from then on
+  cudaStream_t cap = nullptr;   // private stream the graphs are recorded on (capture runs nothing)
   ~Workspace() {
+    if (cap) cudaStreamDestroy(cap);
+    for (auto& e : wide_exec)
+      if (e) cudaGraphExecDestroy(e);
     for (int l = 0; l < 4; ++l) {
       if (side[l]) cudaStreamDestroy(side[l]);
       if (join[l]) cudaEventDestroy(join[l]);
@@ -306,15 +318,13 @@ struct Ctx {
       a.bar.gen = bar + 32;
       a.bar.status = ws->status;
       a.bar.timeout_ns = (long long)timeout_ns;
-      CK(cudaMemsetAsync(bar, 0, sizeof(unsigned) * 64, st));
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       if (o.profile) {
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         CK(cudaEventRecord(e0, st));
       }
-      CK(launch_wide_cg(a, grid, st));
-      after_launch();
+      wide_launch(a, grid, bar);
       if (o.profile) CK(cudaEventRecord(e1, st));
       CK(cudaMemcpyAsync(its.data() + c0, a.it_out, sizeof(int64_t) * mc, cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(cv.data() + c0, a.conv, sizeof(int) * mc, cudaMemcpyDeviceToHost, st));
@@ -336,6 +346,52 @@ struct Ctx {
         S.pcg_flops += (double)itsum * (2.0 * zA + 10.0 * nn);
       }
     }
+  }
+
+  // The barrier reset and the wide launch as one CUDA graph: recorded on a
+  // private stream at the first call with a given argument set (the
+  // refinement reuses its buffers from iteration to iteration), launched on
+  // the caller's stream then and replayed afterwards; if capture is refused
+  // the two are issued directly from then on.
+  void wide_launch(const WideArgs& a, int grid, unsigned* bar) {
+    if (!ws->wide_graph_off) {
+      for (int i = 0; i < Workspace::kWideGraphs; ++i)
+        if (ws->wide_exec[i] && std::memcmp(&ws->wide_key[i], &a, sizeof(WideArgs)) == 0) {
+          CK(cudaGraphLaunch(ws->wide_exec[i], st));
+          ++S.kernel_launches;
+          ++S.graph_replays;
+          return;
+        }
+      const int slot = ws->wide_next;
+      ws->wide_next = (slot + 1) % Workspace::kWideGraphs;
+      if (ws->wide_exec[slot]) {
+        cudaGraphExecDestroy(ws->wide_exec[slot]);
+        ws->wide_exec[slot] = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      if (!ws->cap) CK(cudaStreamCreateWithFlags(&ws->cap, cudaStreamNonBlocking));
+      bool ok = cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        const bool issued = cudaMemsetAsync(bar, 0, sizeof(unsigned) * 64, ws->cap) == cudaSuccess &&
+                            launch_wide_cg(a, grid, ws->cap) == cudaSuccess;
+        ok = (cudaStreamEndCapture(ws->cap, &g) == cudaSuccess) && issued && g;
+      }
+      cudaGraphExec_t ex = nullptr;
+      if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      if (ok) {
+        ws->wide_exec[slot] = ex;
+        std::memcpy(&ws->wide_key[slot], &a, sizeof(WideArgs));
+        CK(cudaGraphLaunch(ex, st));
+        ++S.kernel_launches;
+        return;
+      }
+      ws->wide_graph_off = true;
+    }
+    CK(cudaMemsetAsync(bar, 0, sizeof(unsigned) * 64, st));
+    CK(launch_wide_cg(a, grid, st));
+    after_launch();
   }
 
   void solve_df(const double* B, double* X, int m, int x0, double tol, int maxit, std::vector<int64_t>* iters,
