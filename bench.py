@@ -30,7 +30,8 @@ Also reported:
                Lanczos (scipy ARPACK) result stored with its input hash;
   * cpu_baseline -- the CPU oracle on a bounded sample of the same workload.
 
-Expected wall time at --steps 20 --warmup 5 (one step ~40 s): about 1100 s.
+Expected wall time at --steps 20 --warmup 5 (one step ~24 s): about 12 minutes;
+the optional legs are skipped once the run would pass --budget-s.
 ``--impl reference`` times the CPU oracle instead (the reference arm).
 Multi-GPU (torchrun): replicas only -- every rank solves its own copy of the
 workload, no data-path collective; value = total eigenpairs / max time.

@@ -361,7 +361,9 @@ const char* mmd_last_error(void);
  * Every call reuses the same array and keeps nothing from the last one:
  * before its kernel it clears, on its stream, what must start at zero (the
  * barrier counter and the status word); calls that can run concurrently on
- * the GPU (unordered streams) race on the array, so order them.  iters may be NULL.  Returns MMD_OK, MMD_EINVAL,
+ * the GPU (unordered streams) race on the array, so order them.  The call is
+ * synchronous: it waits on its stream for the iteration count and status
+ * before it returns.  iters may be NULL.  Returns MMD_OK, MMD_EINVAL,
  * MMD_ENOCONV (max_iter reached, x holds the last iterate), MMD_ENOTSPD,
  * MMD_ETIMEOUT or MMD_ECUDA. */
 #define MMD_NOALLOC_MAX_N 262144
