@@ -1,6 +1,7 @@
 """Host logic of bench.py on the CPU: the clock summary that decides whether a
 timed run is kept (median SM clock under load, throttle reasons seen), the
-HBM peak lookup and the whole-job value.  No GPU, no nvidia-smi."""
+HBM peak lookup, the whole-job value and the reference arm's JSON line.  No
+GPU, no nvidia-smi."""
 import json
 import os
 import sys
@@ -60,3 +61,25 @@ def test_peaks_reads_measured_file(tmp_path, monkeypatch):
 def test_job_value_counts_all_replicas():
     assert bench.job_value(1, 500, 1, 40000.0) == pytest.approx(12.5)
     assert bench.job_value(4, 500, 2, 80000.0) == pytest.approx(50.0)
+
+
+def test_reference_arm_prints_one_complete_line():
+    """The reference arm (the CPU oracle on its bounded sample) runs without a
+    GPU and prints one JSON line with the keys the bench contract asks for."""
+    import subprocess
+
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], capture_output=True, text=True, env=env, cwd=ROOT, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"] == "leftmost eigenpairs/sec to residual 1e-8" and d["unit"] == "eigenpairs/s"
+    assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 3 and d["higher_is_better"] is True
+    assert d["config"]["workload"] == bench.WORKLOAD["workload"]
+    assert d["config"]["sample"]["npts"] == bench.SAMPLE["npts"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
