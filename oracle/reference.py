@@ -8,8 +8,9 @@ dense eigensolver this module computes the N smallest eigenvalues by a
 different algorithm that shares nothing with the hierarchy: shift-invert
 Lanczos (ARPACK, scipy.sparse.linalg.eigsh) about sigma = 0 with the exact
 inverse from a sparse LU factorisation of A (SuperLU, symmetric ordering on
-the pattern of A + A^T, diagonal pivots).  It is the survey's "independent
-check for n > 2000"; the tests pin it against dense LAPACK at small n.
+the pattern of A + A^T, diagonal pivots).  It is the independent check of
+the final result where n is above 2000; the tests pin it against dense
+LAPACK at small n.
 """
 from __future__ import annotations
 
