@@ -1,4 +1,5 @@
-"""Full-size check on the benchmark's workload: the 500 leftmost eigenpairs
+"""Full-size checks.  The 3D FD workload's SpMV (128^3 cells) against the CSR
+product on every row; and the benchmark's workload: the 500 leftmost eigenpairs
 of the torus kNN 200k Laplacian (+1e-6 I) from eig_leftmost, in the launch
 configuration bench.py times (default options, FP64, tol 1e-8), against an
 independent result stored in tests/golden/torus_knn_200k_eigs.json (shift-
@@ -51,6 +52,27 @@ def test_torus_knn_200k_matches_independent_reference():
     assert st["n_converged"] == N and st["max_rel_residual"] <= tol
     G = (V @ V.T).cpu().numpy()
     assert np.abs(G - np.eye(N)).max() <= 1e-10
+    h.close()
+
+
+def test_fd3d_128_spmv_config_matches_csr_product():
+    """The 3D FD workload at its full size (128^3 cells, n = 2,097,152,
+    nnz = 14,581,760, a = 10^U(-3,3) with inclusion boxes at 1e4): the
+    library's FP64 SELL SpMV (the kernel and matrix of the bench's HBM figure)
+    against the CSR product y = A x on every row, at 1e-12 of max |y| (same
+    products, different summation order)."""
+    import torch
+
+    import paper_1804_03415_gb300 as pkg
+
+    A = W.fd3d(128, seed=W.BASE_SEED + 2)
+    assert A.n == 128 ** 3 and A.nnz == 14_581_760
+    x = np.random.default_rng(11).standard_normal(A.n)
+    h = pkg.MMD(A.rowptr, A.col, A.val, k_max=0)
+    y = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    h.level_spmv(0, 0, torch.from_numpy(x).cuda(), y)
+    ref = A.to_scipy() @ x
+    assert np.abs(y.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
     h.close()
 
 
