@@ -47,6 +47,30 @@ def test_workload_sizes():
     assert A.n == 16**3 and A.nnz == 16**3 + 6 * 16 * 16 * 15
 
 
+def test_stored_large_reference_matches_the_generator():
+    """The stored shift-invert reference of the torus kNN 200k workload was
+    computed for the matrix the generator still produces (same integer
+    pattern; values equal up to last-bit differences of exp()), a Laplacian
+    plus 1e-6 I (all entries sum to 1e-6 n), and its eigenvalues are ascending,
+    start at the shifted zero mode of the connected graph, and lie below the
+    infinity-norm bound."""
+    import hashlib
+
+    ref = json.load(open(os.path.join(GOLDEN, "torus_knn_200k_eigs.json")))
+    A = W.torus_knn(200_000, k=10, seed=W.BASE_SEED + 1)
+    assert (A.n, A.nnz) == (ref["n"], ref["nnz"])
+    hp = hashlib.sha256()
+    for arr in (A.rowptr, A.col):
+        hp.update(np.ascontiguousarray(arr).tobytes())
+    assert hp.hexdigest() == ref["pattern_sha256"]
+    assert abs(float(np.sum(A.val ** 2)) - ref["val_sq_sum"]) <= 1e-12 * ref["val_sq_sum"]
+    assert abs(float(np.sum(A.val)) - 1e-6 * A.n) <= 1e-8
+    lam = np.asarray(ref["eigenvalues"])
+    assert np.all(np.diff(lam) >= 0)
+    assert abs(lam[0] - 1e-6) <= 1e-12 and lam[1] > 10 * lam[0]
+    assert lam[-1] <= ref["norm_A_inf"]
+
+
 def test_path_graph_spectrum():
     n = 40
     ev = np.linalg.eigvalsh(W.path_graph(n).dense())
